@@ -1,0 +1,245 @@
+"""Multigrid preconditioner with the colourised vertex-patch smoother and the
+outer flexible CG (paper Sec. 3, Sec. 3.1 Algorithm 1, Eqs. residual and
+local-solver; Sec. 3.3 for the iteration count nu).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Readings of the paper (listed in the design doc):
+  * level l has N_l = N_L / 2^(L-l) cells per direction; the coarsest level
+    is solved exactly (P_0^{-1} = A_0^{-1}, Sec. 3);
+  * coarse operators are re-discretised SIPG matrices with their own h;
+  * prolongation is the canonical embedding (Sec. 3): fine nodal values are
+    the coarse polynomial evaluated at the fine nodes; restriction of
+    residuals is its transpose P^T (the L2-projection of Sec. 3 seen on dual
+    vectors);
+  * one patch per interior vertex, the 2^d cells sharing it (Sec. 3.1);
+  * Dirichlet kernel space V_j: all nodes of the patch cells except the
+    nodes on the patch boundary (Sec. 3.1); a patch-boundary end that lies on
+    the domain boundary is kept in V_j (the paper is silent);
+  * "consistent" local residual r_j = R_j (b - A x) (default), or the paper's
+    Dirichlet-kernel residual r_j = R_j b - Abar_j Rbar_j x with only the patch
+    cells in the domain of dependence ("paper");
+  * colours: c = sum_e (v_e mod 2) 2^e for vertex index v; pre-smoothing visits
+    colours 0..2^d-1, post-smoothing visits them in reverse;
+  * outer solver: flexible CG with beta = <z_{i+1}, r_{i+1} - r_i> / <z_i, r_i>,
+    stopped at ||r||_2 / ||b||_2 <= rtol (Euclidean norm, Sec. 3.3).
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .assembly import assemble
+from .basis import gauss_lobatto, lagrange_values, tensor_index
+from .layout import cell_multi_index, dof_index
+
+
+# ---------------------------------------------------------------- transfer
+def prolongation(dim, k, Nc):
+    """Sparse P from the coarse mesh (Nc^d cells) to the fine mesh (2Nc)^d:
+    P[(f, I), (C, J)] = Phi_J(y_I) where fine cell f = 2C + o, o in {0,1}^d,
+    and y_I = (o + xi_I) / 2 are the fine node coordinates in the coarse
+    reference cell (canonical embedding, Sec. 3)."""
+    n = k + 1
+    nodes, _ = gauss_lobatto(k)
+    loc = tensor_index(dim, n)                 # (n^d, d)
+    Nf = 2 * Nc
+    coarse = cell_multi_index(dim, Nc)
+    offsets = tensor_index(dim, 2)
+    R, C, V = [], [], []
+    for o in offsets:
+        y = (o[None, :] + nodes[loc]) / 2.0   # (n^d, d) fine nodes in coarse coords
+        E = np.ones((n ** dim, n ** dim))      # E[I, J] = Phi_J(y_I)
+        for e in range(dim):
+            E *= lagrange_values(nodes, y[:, e])[:, loc[:, e]]
+        fine = 2 * coarse + o[None, :]
+        r = dof_index(dim, Nf, n, fine[:, None, :], np.arange(n ** dim)[None, :])
+        c = dof_index(dim, Nc, n, coarse[:, None, :], np.arange(n ** dim)[None, :])
+        F = len(coarse)
+        R.append(np.broadcast_to(r[:, :, None], (F, n ** dim, n ** dim)).ravel())
+        C.append(np.broadcast_to(c[:, None, :], (F, n ** dim, n ** dim)).ravel())
+        V.append(np.broadcast_to(E[None], (F, n ** dim, n ** dim)).ravel())
+    P = sp.coo_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(C))),
+                      shape=(Nf ** dim * n ** dim, Nc ** dim * n ** dim)).tocsr()
+    P.eliminate_zeros()
+    return P
+
+
+# ---------------------------------------------------------------- patches
+def vertex_patches(dim, k, N, variant="consistent"):
+    """All vertex patches of the N^d mesh (one per interior vertex).
+
+    Returns a list of dicts with keys
+      vertex  : vertex multi-index v (each v_e in 1..N-1)
+      colour  : sum_e (v_e mod 2) 2^e
+      V       : sorted global DoF indices of the Dirichlet-kernel space V_j
+      dofs    : all DoF indices of the 2^d patch cells (domain of dependence
+                of the paper's Dirichlet kernel)
+      type    : per direction (v_e == 1, v_e == N-1)
+    """
+    n = k + 1
+    nloc = n ** dim
+    loc = tensor_index(dim, n)
+    offsets = tensor_index(dim, 2)
+    patches = []
+    for v in tensor_index(dim, N - 1) + 1:
+        keepV, alld = [], []
+        for o in offsets:
+            cell = v - 1 + o
+            g = dof_index(dim, N, n, cell[None, :], np.arange(nloc))
+            a = o[None, :] * n + loc                  # 1D patch coordinates 0..2n-1
+            inside = np.ones(nloc, dtype=bool)
+            for e in range(dim):
+                left_ok = (a[:, e] != 0) | (v[e] == 1)
+                right_ok = (a[:, e] != 2 * n - 1) | (v[e] == N - 1)
+                inside &= left_ok & right_ok
+            keepV.append(g[inside])
+            alld.append(g)
+        patches.append(dict(
+            vertex=tuple(int(t) for t in v),
+            colour=int(sum((int(v[e]) % 2) << e for e in range(dim))),
+            V=np.sort(np.concatenate(keepV)),
+            dofs=np.sort(np.concatenate(alld)),
+            type=tuple((bool(v[e] == 1), bool(v[e] == N - 1)) for e in range(dim)),
+        ))
+    return patches
+
+
+class Level:
+    """One level of the hierarchy: matrix, patches and their local solvers."""
+
+    def __init__(self, dim, k, N, kappa=1.0, eta=1.0, variant="consistent"):
+        self.dim, self.k, self.N = dim, k, N
+        self.variant = variant
+        self.A = assemble(dim, k, N, kappa, eta)
+        self.ndof = self.A.shape[0]
+        self.patches = vertex_patches(dim, k, N)
+        for p in self.patches:
+            V = p["V"]
+            Aj = self.A[V][:, V].toarray()           # A_j = R_j A R_j^T
+            p["chol"] = sla.cho_factor(Aj, lower=True)
+            if variant == "consistent":
+                p["rows"] = self.A[V]                # all columns: R_j A
+                p["cols"] = None
+            elif variant == "paper":
+                p["rows"] = self.A[V][:, p["dofs"]]  # Abar_j: patch columns only
+                p["cols"] = p["dofs"]
+            else:
+                raise ValueError(variant)
+
+    def colour_order(self, reverse=False):
+        order = list(range(2 ** self.dim))
+        return order[::-1] if reverse else order
+
+
+def local_residual(patch, b, x):
+    """r_j of Algorithm 1 (consistent: R_j (b - A x); paper: R_j b - Abar_j Rbar_j x)."""
+    V = patch["V"]
+    if patch["cols"] is None:
+        return b[V] - patch["rows"] @ x
+    return b[V] - patch["rows"] @ x[patch["cols"]]
+
+
+def smooth(level, x, b, reverse=False, patch_order=None, colours=None):
+    """One step of the colourised multiplicative vertex-patch smoother
+    S_l(x, b) (Algorithm 1): colours in sequence; inside a colour, patches
+    one after another (the paper's parallel loop; the tests check that the
+    order inside a colour does not change the result), each doing
+    r_j <- local residual; x <- x + R_j^T A_j^{-1} r_j.
+    ``colours`` restricts the sweep to the listed colours (in that order)."""
+    x = np.array(x, dtype=np.float64, copy=True)
+    order = level.colour_order(reverse) if colours is None else list(colours)
+    for c in order:
+        members = [p for p in level.patches if p["colour"] == c]
+        if patch_order is not None:
+            members = [members[i] for i in patch_order(c, len(members))]
+        for p in members:
+            r = local_residual(p, b, x)
+            x[p["V"]] += sla.cho_solve(p["chol"], r)
+    return x
+
+
+class Hierarchy:
+    """Mesh hierarchy T_0 < ... < T_L with N_l = N_L / 2^(L-l) (Sec. 3)."""
+
+    def __init__(self, dim, k, N, n_levels, kappa=1.0, eta=1.0, variant="consistent"):
+        if N % (1 << (n_levels - 1)) != 0 or N >> (n_levels - 1) < 2:
+            raise ValueError("coarsest level needs >= 2 cells per direction")
+        self.dim, self.k, self.N, self.L = dim, k, N, n_levels - 1
+        self.levels = []
+        self.P = [None]
+        for l in range(n_levels):
+            Nl = N >> (self.L - l)
+            self.levels.append(Level(dim, k, Nl, kappa, eta, variant))
+            if l > 0:
+                self.P.append(prolongation(dim, k, Nl // 2))
+        A0 = self.levels[0].A.toarray()
+        self.coarse = sla.cho_factor(A0, lower=True)
+
+    def vcycle(self, b, l=None):
+        """Action of the multigrid preconditioner P_l^{-1} on b (Sec. 3):
+        pre-smoothing from x = 0, coarse-grid correction
+        x += I^up P_{l-1}^{-1} I^down (b - A_l x), post-smoothing (reversed
+        colours); P_0^{-1} = A_0^{-1}."""
+        if l is None:
+            l = self.L
+        if l == 0:
+            return sla.cho_solve(self.coarse, b)
+        lev = self.levels[l]
+        x = np.zeros(lev.ndof)
+        x = smooth(lev, x, b, reverse=False)
+        r = b - lev.A @ x
+        rc = self.P[l].T @ r
+        ec = self.vcycle(rc, l - 1)
+        x = x + self.P[l] @ ec
+        x = smooth(lev, x, b, reverse=True)
+        return x
+
+    @property
+    def A(self):
+        return self.levels[-1].A
+
+
+def fcg(A_apply, precond, b, rtol=1e-10, maxit=200, x0=None):
+    """Flexible preconditioned CG (Polak-Ribiere form):
+      r_0 = b - A x_0, z_0 = B r_0, p_0 = z_0;
+      alpha_i = <r_i, z_i> / <p_i, A p_i>; x += alpha p; r -= alpha A p;
+      z_{i+1} = B r_{i+1}; beta_i = <z_{i+1}, r_{i+1} - r_i> / <z_i, r_i>;
+      p_{i+1} = z_{i+1} + beta_i p_i.
+    Stops when ||r||_2 <= rtol ||b||_2.  Returns (x, history of ||r||_2)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - A_apply(x)
+    bnorm = np.linalg.norm(b)
+    hist = [np.linalg.norm(r)]
+    if bnorm == 0.0 or hist[0] <= rtol * bnorm:
+        return x, hist
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    for _ in range(maxit):
+        q = A_apply(p)
+        alpha = rz / (p @ q)
+        x = x + alpha * p
+        r_new = r - alpha * q
+        hist.append(np.linalg.norm(r_new))
+        if hist[-1] <= rtol * bnorm:
+            break
+        z_new = precond(r_new)
+        beta = (z_new @ (r_new - r)) / rz
+        p = z_new + beta * p
+        r, z = r_new, z_new
+        rz = r @ z
+    return x, hist
+
+
+def mg_solve(hier, b, rtol=1e-10, maxit=200, x0=None):
+    """MG-preconditioned flexible CG on the finest level."""
+    A = hier.A
+    return fcg(lambda v: A @ v, hier.vcycle, b, rtol, maxit, x0)
+
+
+def fractional_iterations(hist, digits=8):
+    """nu = -digits * log10(rbar), rbar = (||r_n|| / ||r_0||)^(1/n) (Sec. 3.3)."""
+    n = len(hist) - 1
+    rbar = (hist[-1] / hist[0]) ** (1.0 / n)
+    return -digits / np.log10(rbar)
