@@ -1,0 +1,207 @@
+/*
+ * sipg.h -- C ABI of the GB300 (sm_103a) matrix-free multigrid library for the
+ * symmetric interior penalty (SIPG) DG discretisation of the Poisson problem
+ * on Cartesian meshes of the unit square / cube, after Cui & Kanschat,
+ * "Multilevel Interior Penalty Methods on GPUs" (arXiv 2405.18982).
+ *
+ * Problem (Sec. 2, Eqs. model, bilinear_form, weak_form, mat_form):
+ *   find u_h in V_h (discontinuous Q_k, Lagrange basis on Gauss-Lobatto
+ *   points, Appendix A) with kappa * a_h(u_h, v) = (f, v) for all v, a_h the
+ *   SIPG form with penalty gamma_e = eta k(k+1)(1/h+ + 1/h-), also on
+ *   boundary faces (h- := h+), homogeneous Dirichlet conditions imposed
+ *   weakly.  Matrix form A x = b.
+ *
+ * Solver (Sec. 3): flexible CG on the finest level, preconditioned by one
+ * multigrid V-cycle (Sec. 3) with the colourised multiplicative vertex-patch
+ * smoother (Algorithm 1), fast-diagonalisation local solvers (Eqs. inverse2d,
+ * inverse3d, fast_inverse), canonical-embedding prolongation and its
+ * transpose as restriction, and an exact coarse solve.  The V-cycle may run
+ * in FP32 inside the FP64 outer solver (Sec. 5.2).
+ *
+ * Data layout (Sec. 4.1): every vector is cell-wise lexicographic.  On a level
+ * with N cells per direction and n = k+1 nodes per direction, DoF (cell c,
+ * local node i) is at index c * n^d + i with c = c0 + N (c1 + N c2) and
+ * i = i0 + n (i1 + n i2), index 0 fastest.  With nrhs > 1 the right-hand
+ * sides are stored one after another: column r starts at r * n_dofs.
+ *
+ * Memory and streams: the caller owns all device memory.  sipg_create only
+ * validates parameters and sizes; the caller then allocates
+ * sipg_workspace_bytes() bytes of device memory (256-byte aligned) and binds
+ * it with sipg_bind_workspace(), which runs the device-side level setup.  No
+ * entry point allocates device memory.  Vector arguments are device pointers
+ * unless stated otherwise, must be 16-byte aligned and must not alias unless
+ * stated.  `stream` is a cudaStream_t (NULL = legacy default stream); all work
+ * is ordered on it.  Only sipg_solve, sipg_adjoint_solve and
+ * sipg_solve_host synchronise (their stream), because convergence is decided
+ * on the host.
+ *
+ * Errors: every call returns a sipg_status; failures never abort or trap.
+ * sipg_last_error(h) returns a message for the last failure on h.
+ */
+#ifndef SIPG_H
+#define SIPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SIPG_OK = 0,
+  SIPG_EINVAL = -1,           /* bad argument (null pointer, size, range)           */
+  SIPG_ENOMEM_WORKSPACE = -2, /* workspace missing or too small                      */
+  SIPG_ECUDA = -3,            /* a CUDA runtime call failed                          */
+  SIPG_ENOCONV = -4,          /* solver hit maxit before rtol                        */
+  SIPG_EBREAKDOWN = -5,       /* non-finite or non-positive Krylov scalar            */
+  SIPG_ETIMEOUT = -6,         /* a bounded device-side wait ran out                  */
+  SIPG_EUNSUPPORTED = -7,     /* valid but unsupported configuration                 */
+  SIPG_ESTATE = -8            /* call out of order (e.g. workspace not bound)        */
+} sipg_status;
+
+/* Arithmetic of the V-cycle (operator apply, smoother, transfer); the outer
+ * Krylov solver, its residual, dot products and updates, the 1D eigenpair
+ * setup and the coarse solve are always FP64. */
+typedef enum {
+  SIPG_FP64 = 0,
+  SIPG_FP32 = 1
+} sipg_precision;
+
+/* Local residual of the Dirichlet-kernel patch solver (Sec. 3.1). */
+typedef enum {
+  /* r_j = R_j (b - A x): exact residual, including the face-node layer of
+   * the cells around the patch (default; symmetric V-cycle). */
+  SIPG_SMOOTHER_CONSISTENT = 0,
+  /* r_j = R_j b - Abar_j Rbar_j x with only the patch cells (the paper's
+   * Dirichlet kernel, inconsistent residual). */
+  SIPG_SMOOTHER_PAPER = 1
+} sipg_smoother;
+
+typedef struct {
+  int dim;               /* 2 or 3                                                       */
+  int degree;            /* k, 1..7                                                      */
+  int log2_cells;        /* finest level has N = 2^log2_cells cells per direction        */
+  int n_levels;          /* >= 1; level l has N >> (n_levels-1-l) cells, coarsest >= 2  */
+  double kappa;          /* > 0, scalar diffusion coefficient multiplying the form      */
+  double penalty_factor; /* eta > 0; gamma_e = eta k(k+1)(1/h+ + 1/h-) (paper: eta = 1) */
+  int vcycle_precision;  /* sipg_precision                                               */
+  int smoother;          /* sipg_smoother                                                */
+  int nrhs;              /* >= 1 right-hand sides solved together                        */
+  int use_graphs;        /* != 0: capture one Krylov iteration in a CUDA graph           */
+} sipg_params;
+
+typedef struct {
+  int iterations;        /* outer FCG iterations done                                   */
+  int status;            /* sipg_status of the solve                                    */
+  double rel_residual;   /* max over rhs of ||b - A x||_2 / ||b||_2 (true residual)     */
+  double nu;             /* fractional iteration count of Sec. 3.3 (8 digits), rhs 0    */
+  double* history;       /* caller buffer (host) or NULL: ||r_i||_2 of rhs 0 per iter   */
+  int history_capacity;  /* entries available in history                                */
+  int history_len;       /* entries written                                             */
+} sipg_info;
+
+typedef struct sipg_handle sipg_handle;
+
+/* Validate params and compute sizes; no CUDA call.  *out = NULL on error. */
+sipg_status sipg_create(const sipg_params* params, sipg_handle** out);
+void sipg_destroy(sipg_handle* h);
+const char* sipg_last_error(const sipg_handle* h);
+const char* sipg_version(void);
+
+/* Bytes of device workspace the handle needs (level vectors, Krylov vectors,
+ * reduction scratch, level constants). */
+size_t sipg_workspace_bytes(const sipg_handle* h);
+/* Bind caller-owned device memory (256-byte aligned, >= workspace bytes) and
+ * run the FP64 device setup of all levels on `stream` (1D Gauss-Lobatto
+ * basis, 1D SIPG blocks, patch eigenpairs of Eq. fast_inverse by Cholesky and
+ * cyclic Jacobi, coarse-level eigenpairs, transfer matrices).  May be called
+ * again with another buffer; the handle then uses the new one. */
+sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, void* stream);
+
+/* Number of DoFs of one right-hand side on `level` (0 = coarsest). */
+size_t sipg_ndofs(const sipg_handle* h, int level);
+/* Launches of library kernels issued since creation (kernels inside a CUDA
+ * graph launch are counted once per graph launch). */
+uint64_t sipg_launch_count(const sipg_handle* h);
+
+/* b = M_h f on the finest level (Eq. weak_form with f given by nodal values
+ * in V_h): the exact block-diagonal mass applied cell by cell.  FP64, nrhs
+ * columns.  Also serves as dJ/df = M_h lambda in the adjoint. */
+sipg_status sipg_rhs(sipg_handle* h, const double* f, double* b, void* stream);
+
+/* f = d pi^2 prod_e sin(pi x_e) at the nodes of the finest level (the
+ * manufactured source of u = prod_e sin(pi x_e)), written to every column. */
+sipg_status sipg_manufactured_source(sipg_handle* h, double* f, void* stream);
+
+/* y = A_level x (Eq. mat_form on that level, Sec. 2.2 matrix-free,
+ * sum-factorised).  prec selects double* or float* vectors. nrhs columns. */
+sipg_status sipg_apply(sipg_handle* h, int level, int prec, const void* x, void* y, void* stream);
+/* r = b - A_level x (fused). r may alias b. */
+sipg_status sipg_residual(sipg_handle* h, int level, int prec, const void* b, const void* x,
+                          void* r, void* stream);
+/* y = (dA/dgamma) x on the finest level: the penalty face terms with unit
+ * penalty, times kappa (derivative with respect to the uniform fine-level
+ * face penalty gamma). FP64. */
+sipg_status sipg_apply_penalty(sipg_handle* h, const double* x, double* y, void* stream);
+
+/* One colour pass of Algorithm 1 on `level`: for all vertex patches j of
+ * colour c (c = sum_e (v_e mod 2) 2^e, v the vertex index), in parallel,
+ * r_j = local residual, x[V_j] += (S (x) S (x) S) Lambda^{-1} (S^T (x) ...) r_j.
+ * x is updated in place. */
+sipg_status sipg_smooth_colour(sipg_handle* h, int level, int prec, int colour, const void* b,
+                               void* x, void* stream);
+/* One smoothing step S_l(x, b): colours 0..2^d-1, or 2^d-1..0 if reverse. */
+sipg_status sipg_smooth(sipg_handle* h, int level, int prec, int reverse, const void* b, void* x,
+                        void* stream);
+/* r_coarse = P^T r_fine between level `fine_level` and fine_level-1
+ * (transpose of the canonical embedding, Sec. 3). */
+sipg_status sipg_restrict(sipg_handle* h, int fine_level, int prec, const void* r_fine,
+                          void* r_coarse, void* stream);
+/* x_fine += P e_coarse (canonical embedding, Sec. 3). */
+sipg_status sipg_prolongate_add(sipg_handle* h, int fine_level, int prec, const void* e_coarse,
+                                void* x_fine, void* stream);
+/* x0 = A_0^{-1} b0 on the coarsest level, exact, FP64 arithmetic (global fast
+ * diagonalisation); prec selects the vector type. */
+sipg_status sipg_coarse_solve(sipg_handle* h, int prec, const void* b0, void* x0, void* stream);
+/* x = P_L^{-1} b: one V-cycle from x = 0 (Sec. 3), 1 pre- and 1
+ * post-smoothing step (post-smoothing visits the colours in reverse).
+ * prec = vector type of b and x; with SIPG_FP32 the whole V-cycle except the
+ * coarse solve runs in FP32. */
+sipg_status sipg_vcycle(sipg_handle* h, int prec, const void* b, void* x, void* stream);
+
+/* Flexible CG on the finest level with the V-cycle (params.vcycle_precision)
+ * as preconditioner, until ||b - A x||_2 <= rtol ||b||_2 for every column or
+ * maxit iterations.  b, x: FP64, nrhs columns; x holds the initial guess on
+ * entry and the solution on exit.  info may be NULL.  Synchronises stream. */
+sipg_status sipg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
+                       sipg_info* info, void* stream);
+/* Adjoint solve A^T lambda = g.  The SIPG matrix is symmetric, so this is
+ * the same MG-preconditioned FCG applied to g. */
+sipg_status sipg_adjoint_solve(sipg_handle* h, const double* g, double* lambda, double rtol,
+                               int maxit, sipg_info* info, void* stream);
+/* Same as sipg_solve with HOST buffers f (nodal source, FP64, nrhs columns)
+ * and u (solution): copies f in, forms b = M_h f, solves from x = 0, copies u
+ * out, all on `stream`.  Synchronises stream. */
+sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host, double rtol,
+                            int maxit, sipg_info* info, void* stream);
+
+/* out[r] = <a_r, b_r> for every column r (FP64, deterministic order),
+ * written to device memory. */
+sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* out, void* stream);
+
+/* Copy FP64 level constants to host memory for inspection.  which:
+ *  0 Lself (3 x n x n), 1 neighbour blocks [l_lo, l_hi] (2 x n x n),
+ *  2 cell mass (n x n), 3 patch eigenvectors S of type t (p x p),
+ *  4 patch eigenvalues of type t (p), 5 transfer [P_0, P_1] (2 x n x n),
+ *  6 coarse eigenvectors (m0 x m0), 7 coarse eigenvalues (m0),
+ *  8 Gauss-Lobatto nodes (n).  `type` is the patch type for 3/4 (bit 0: low
+ * end on the boundary, bit 1: high end).  Writes at most cap doubles; returns
+ * the count in *count.  Synchronises stream. */
+sipg_status sipg_get_constants(sipg_handle* h, int level, int which, int type, double* host_out,
+                               int cap, int* count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIPG_H */

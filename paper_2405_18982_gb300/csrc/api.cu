@@ -1,0 +1,648 @@
+// C ABI of the library (declared in include/sipg.h): handle and workspace
+// management, the V-cycle of Sec. 3 and the flexible CG outer solver.
+// All device memory is caller-owned; every kernel launch is ordered on the
+// caller's stream (or, for CUDA-graph replay, on an internal stream joined to
+// it by events).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sipg_internal.cuh"
+
+namespace {
+
+const char* kVersion = "sipg-gb300 0.1 (sm_103a)";
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+sipg_status fail(sipg_handle* h, sipg_status st, const char* msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+sipg_status cuda_fail(sipg_handle* h, cudaError_t e, const char* where) {
+  if (h) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    h->err = buf;
+  }
+  return SIPG_ECUDA;
+}
+
+#define SIPG_CHECK(expr, where)                 \
+  do {                                          \
+    cudaError_t e_ = (expr);                    \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+sipg_status need_bound(sipg_handle* h) {
+  if (!h) return SIPG_EINVAL;
+  if (!h->bound) return fail(h, SIPG_ESTATE, "workspace not bound");
+  return SIPG_OK;
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+size_t vec_bytes(const sipg_handle* h, int level, size_t elem) {
+  return align256(h->lv[level].ndofs * (size_t)h->prm.nrhs * elem);
+}
+
+// ------------------------------------------------------------------ V-cycle
+template <typename T>
+sipg_status smooth_T(sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s) {
+  const int nc = 1 << h->prm.dim;
+  for (int i = 0; i < nc; ++i) {
+    int c = reverse ? nc - 1 - i : i;
+    SIPG_CHECK(launch_smooth_colour<T>(h, level, c, b, x, s), "smoother");
+    h->launches += 1;
+  }
+  return SIPG_OK;
+}
+
+template <typename T>
+sipg_status vcycle_T(sipg_handle* h, const T* bL, T* xL, cudaStream_t s) {
+  const int L = h->L;
+  const int nr = h->prm.nrhs;
+  auto bvec = [&](int l) -> T* { return (l == L) ? const_cast<T*>(bL) : reinterpret_cast<T*>(h->vb(l)); };
+  auto xvec = [&](int l) -> T* { return (l == L) ? xL : reinterpret_cast<T*>(h->vx(l)); };
+  for (int l = L; l >= 1; --l) {
+    T* b = bvec(l);
+    T* x = xvec(l);
+    SIPG_CHECK(cudaMemsetAsync(x, 0, h->lv[l].ndofs * nr * sizeof(T), s), "memset");
+    sipg_status st = smooth_T<T>(h, l, 0, b, x, s);
+    if (st) return st;
+    T* r = reinterpret_cast<T*>(h->vr(l));
+    SIPG_CHECK(launch_apply<T>(h, l, APPLY_RESIDUAL, b, x, r, s), "residual");
+    SIPG_CHECK(launch_restrict<T>(h, l, r, bvec(l - 1), s), "restrict");
+    h->launches += 2;
+  }
+  SIPG_CHECK(launch_coarse_solve<T>(h, bvec(0), xvec(0), s), "coarse solve");
+  h->launches += 1;
+  for (int l = 1; l <= L; ++l) {
+    SIPG_CHECK(launch_prolongate_add<T>(h, l, xvec(l - 1), xvec(l), s), "prolongate");
+    h->launches += 1;
+    sipg_status st = smooth_T<T>(h, l, 1, bvec(l), xvec(l), s);
+    if (st) return st;
+  }
+  return SIPG_OK;
+}
+
+// z = B r for the Krylov residual in kr(); leaves the preconditioned vector
+// either in kz() (FP64 V-cycle) or in the FP32 finest-level buffer.
+sipg_status precondition(sipg_handle* h, int first, cudaStream_t s) {
+  sipg_status st;
+  if (h->prm.vcycle_precision == SIPG_FP32) {
+    float* bL = reinterpret_cast<float*>(h->ws + h->off_bL);
+    float* xL = reinterpret_cast<float*>(h->ws + h->off_xL);
+    if (first) {
+      SIPG_CHECK(convert_d2f(h->kr(), bL, h->lv[h->L].ndofs * h->prm.nrhs, s), "convert");
+      h->launches += 1;
+    }
+    st = vcycle_T<float>(h, bL, xL, s);
+    if (st) return st;
+    SIPG_CHECK(krylov_after_precond(h, first, h->kr(), xL, 1, s), "precond post");
+  } else {
+    st = vcycle_T<double>(h, h->kr(), h->kz(), s);
+    if (st) return st;
+    SIPG_CHECK(krylov_after_precond(h, first, h->kr(), h->kz(), 0, s), "precond post");
+  }
+  return SIPG_OK;
+}
+
+// q = A p, alpha, x += alpha p, r -= alpha q, ||r||^2 (and the FP32 copy of r).
+sipg_status step_update(sipg_handle* h, double* x, cudaStream_t s) {
+  SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, h->kp(), h->kq(), s), "apply");
+  h->launches += 1;
+  SIPG_CHECK(krylov_after_apply(h, s), "pq");
+  if (h->prm.vcycle_precision == SIPG_FP32)
+    SIPG_CHECK(krylov_update_xr(h, x, h->ws + h->off_bL, 1, s), "update");
+  else
+    SIPG_CHECK(krylov_update_xr(h, x, nullptr, 0, s), "update");
+  return SIPG_OK;
+}
+
+sipg_status iteration_body(sipg_handle* h, double* x, cudaStream_t s) {
+  sipg_status st = precondition(h, 0, s);
+  if (st) return st;
+  return step_update(h, x, s);
+}
+
+sipg_status read_scalars(sipg_handle* h, std::vector<KrylovScalars>& out, cudaStream_t s) {
+  out.resize(h->prm.nrhs);
+  SIPG_CHECK(cudaMemcpyAsync(out.data(), h->scalars(), sizeof(KrylovScalars) * h->prm.nrhs,
+                             cudaMemcpyDeviceToHost, s),
+             "scalars D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  return SIPG_OK;
+}
+
+// Capture one iteration body as a CUDA graph (on the internal stream).
+sipg_status ensure_graph(sipg_handle* h, double* x) {
+  if (h->iter_exec && h->g_x == x) return SIPG_OK;
+  if (h->iter_exec) {
+    cudaGraphExecDestroy(h->iter_exec);
+    h->iter_exec = nullptr;
+  }
+  if (!h->gstream) SIPG_CHECK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking), "stream");
+  if (!h->ev_a) SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming), "event");
+  if (!h->ev_b) SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming), "event");
+  uint64_t before = h->launches;
+  SIPG_CHECK(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  sipg_status st = iteration_body(h, x, h->gstream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->gstream, &graph);
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+  e = cudaGraphInstantiate(&h->iter_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+  h->graph_launches = h->launches - before;
+  h->launches = before;
+  h->g_x = x;
+  return SIPG_OK;
+}
+
+sipg_status run_body(sipg_handle* h, double* x, cudaStream_t s) {
+  if (!h->prm.use_graphs) return iteration_body(h, x, s);
+  sipg_status st = ensure_graph(h, x);
+  if (st) return st;
+  SIPG_CHECK(cudaEventRecord(h->ev_a, s), "event record");
+  SIPG_CHECK(cudaStreamWaitEvent(h->gstream, h->ev_a, 0), "stream wait");
+  SIPG_CHECK(cudaGraphLaunch(h->iter_exec, h->gstream), "graph launch");
+  SIPG_CHECK(cudaEventRecord(h->ev_b, h->gstream), "event record");
+  SIPG_CHECK(cudaStreamWaitEvent(s, h->ev_b, 0), "stream wait");
+  h->launches += h->graph_launches;
+  return SIPG_OK;
+}
+
+sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
+                      sipg_info* info, cudaStream_t s) {
+  const int nr = h->prm.nrhs;
+  h->rtol2 = rtol * rtol;
+  std::vector<KrylovScalars> sc;
+  std::vector<double> hist0;
+  int it = 0;
+  sipg_status result = SIPG_OK;
+  double r0 = 0.0;
+  bool first_start = true;
+  auto any_breakdown = [&]() {
+    for (int c = 0; c < nr; ++c)
+      if (sc[c].breakdown) return true;
+    return false;
+  };
+  auto any_active = [&]() {
+    for (int c = 0; c < nr; ++c)
+      if (sc[c].active) return true;
+    return false;
+  };
+  // true residual r = b - A x and the norms ||b||, ||r|| (sets the active flags)
+  auto true_residual = [&]() -> sipg_status {
+    SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_RESIDUAL, b, x, h->kr(), s), "residual");
+    h->launches += 1;
+    SIPG_CHECK(krylov_init_norms(h, b, h->kr(), s), "norms");
+    return read_scalars(h, sc, s);
+  };
+  sipg_status st = true_residual();
+  if (st) return st;
+  r0 = sqrt(sc[0].rr);
+  hist0.push_back(r0);
+  (void)first_start;
+  // restarts only happen if the recursively updated residual met rtol while
+  // the true one did not
+  for (int restart = 0; restart < 4 && result == SIPG_OK; ++restart) {
+    if (any_breakdown()) {
+      result = SIPG_EBREAKDOWN;
+      break;
+    }
+    if (!any_active() || it >= maxit) break;
+    st = precondition(h, 1, s);  // z_0 = B r_0, p_0 = z_0
+    if (st) return st;
+    st = step_update(h, x, s);
+    if (st) return st;
+    ++it;
+    st = read_scalars(h, sc, s);
+    if (st) return st;
+    hist0.push_back(sqrt(sc[0].rr));
+    while (!any_breakdown() && any_active() && it < maxit) {
+      st = run_body(h, x, s);
+      if (st) return st;
+      ++it;
+      st = read_scalars(h, sc, s);
+      if (st) return st;
+      hist0.push_back(sqrt(sc[0].rr));
+    }
+    if (any_breakdown()) {
+      result = SIPG_EBREAKDOWN;
+      break;
+    }
+    st = true_residual();
+    if (st) return st;
+  }
+  if (result == SIPG_OK && any_breakdown()) result = SIPG_EBREAKDOWN;
+  double worst = 0.0;
+  bool all_conv = true;
+  for (int c = 0; c < nr; ++c) {
+    double rel = sc[c].bb > 0.0 ? sqrt(sc[c].rr / sc[c].bb) : 0.0;
+    worst = std::max(worst, rel);
+    if (sc[c].active) all_conv = false;
+  }
+  if (result == SIPG_OK && !all_conv) result = SIPG_ENOCONV;
+  if (info) {
+    info->iterations = it;
+    info->status = result;
+    info->rel_residual = worst;
+    double nu = 0.0;
+    if (it > 0 && hist0.size() > 1 && hist0.front() > 0.0) {
+      double rbar = pow(hist0.back() / hist0.front(), 1.0 / (double)(hist0.size() - 1));
+      nu = (rbar > 0.0 && rbar < 1.0) ? -8.0 / log10(rbar) : INFINITY;
+    }
+    info->nu = nu;
+    int cnt = 0;
+    if (info->history && info->history_capacity > 0) {
+      cnt = std::min((int)hist0.size(), info->history_capacity);
+      for (int i = 0; i < cnt; ++i) info->history[i] = hist0[i];
+    }
+    info->history_len = cnt;
+  }
+  if (result == SIPG_ENOCONV) h->err = "solver reached maxit before rtol";
+  if (result == SIPG_EBREAKDOWN) h->err = "Krylov breakdown (non-finite or non-positive scalar)";
+  return result;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* sipg_version(void) { return kVersion; }
+
+sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
+  if (!out) return SIPG_EINVAL;
+  *out = nullptr;
+  if (!p) return SIPG_EINVAL;
+  if (p->dim != 2 && p->dim != 3) return SIPG_EINVAL;
+  if (p->degree < 1 || p->degree > 7) return SIPG_EINVAL;
+  if (p->log2_cells < 1 || p->log2_cells > (p->dim == 2 ? 14 : 10)) return SIPG_EINVAL;
+  if (p->n_levels < 1 || p->n_levels > p->log2_cells) return SIPG_EINVAL;
+  if (!(p->kappa > 0.0) || !isfinite(p->kappa)) return SIPG_EINVAL;
+  if (!(p->penalty_factor > 0.0) || !isfinite(p->penalty_factor)) return SIPG_EINVAL;
+  if (p->vcycle_precision != SIPG_FP64 && p->vcycle_precision != SIPG_FP32) return SIPG_EINVAL;
+  if (p->smoother != SIPG_SMOOTHER_CONSISTENT && p->smoother != SIPG_SMOOTHER_PAPER) return SIPG_EINVAL;
+  if (p->nrhs < 1 || p->nrhs > 65535) return SIPG_EINVAL;
+  const int n = p->degree + 1;
+  const int L = p->n_levels - 1;
+  const int N = 1 << p->log2_cells;
+  const int N0 = N >> L;
+  if (N0 < 2) return SIPG_EINVAL;
+  const int m0 = N0 * n;
+  if (m0 > SIPG_MAXM0) return SIPG_EUNSUPPORTED;
+  if (p->dim == 3 && m0 * m0 * m0 > 4096) return SIPG_EUNSUPPORTED;
+  if (p->dim == 2 && m0 * m0 > 4096) return SIPG_EUNSUPPORTED;
+
+  sipg_handle* h = new sipg_handle();
+  h->prm = *p;
+  h->n = n;
+  h->L = L;
+  for (int l = 0; l <= L; ++l) {
+    LevelInfo li;
+    li.N = N >> (L - l);
+    li.ncells = 1;
+    for (int e = 0; e < p->dim; ++e) li.ncells *= (size_t)li.N;
+    size_t nd = 1;
+    for (int e = 0; e < p->dim; ++e) nd *= (size_t)n;
+    li.ndofs = li.ncells * nd;
+    h->lv.push_back(li);
+  }
+  // workspace layout
+  size_t off = 0;
+  const int nl = L + 1;
+  h->off_const64 = off;
+  off += align256(sizeof(LevelConst<double>) * nl);
+  h->off_const32 = off;
+  off += align256(sizeof(LevelConst<float>) * nl);
+  h->off_scratch_setup = off;
+  off += align256(256 + 5 * SIPG_MAXM0 * SIPG_MAXM0 * sizeof(double));
+  h->n_partials = 1024;
+  h->off_partials = off;
+  off += align256(sizeof(double) * 3 * h->n_partials * p->nrhs);
+  h->off_scalars = off;
+  off += align256(sizeof(KrylovScalars) * p->nrhs);
+  h->off_kr = off;
+  off += vec_bytes(h, L, 8);
+  h->off_kz = off;
+  off += vec_bytes(h, L, 8);
+  h->off_kp = off;
+  off += vec_bytes(h, L, 8);
+  h->off_kq = off;
+  off += vec_bytes(h, L, 8);
+  h->off_hb = off;
+  off += vec_bytes(h, L, 8);
+  h->off_hx = off;
+  off += vec_bytes(h, L, 8);
+  h->off_b.resize(nl);
+  h->off_x.resize(nl);
+  h->off_r.resize(nl);
+  // level vectors sized for FP64 so that any precision can use them
+  for (int l = 0; l <= L; ++l) {
+    h->off_b[l] = off;
+    off += vec_bytes(h, l, 8);
+    h->off_x[l] = off;
+    off += vec_bytes(h, l, 8);
+    h->off_r[l] = off;
+    off += vec_bytes(h, l, 8);
+  }
+  h->off_bL = h->off_b[L];
+  h->off_xL = h->off_x[L];
+  h->ws_bytes = off;
+  *out = h;
+  return SIPG_OK;
+}
+
+void sipg_destroy(sipg_handle* h) {
+  if (!h) return;
+  if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
+  if (h->ev_a) cudaEventDestroy(h->ev_a);
+  if (h->ev_b) cudaEventDestroy(h->ev_b);
+  delete h;
+}
+
+const char* sipg_last_error(const sipg_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+size_t sipg_workspace_bytes(const sipg_handle* h) { return h ? h->ws_bytes : 0; }
+
+size_t sipg_ndofs(const sipg_handle* h, int level) {
+  if (!h || level < 0 || level > h->L) return 0;
+  return h->lv[level].ndofs;
+}
+
+uint64_t sipg_launch_count(const sipg_handle* h) { return h ? h->launches : 0; }
+
+sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, void* stream) {
+  if (!h) return SIPG_EINVAL;
+  if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 255))
+    return fail(h, SIPG_EINVAL, "workspace pointer null or not 256-byte aligned");
+  if (bytes < h->ws_bytes) return fail(h, SIPG_ENOMEM_WORKSPACE, "workspace too small");
+  if (h->iter_exec) {
+    cudaGraphExecDestroy(h->iter_exec);
+    h->iter_exec = nullptr;
+  }
+  h->ws = reinterpret_cast<char*>(dev_ptr);
+  h->bound = true;
+  cudaStream_t s = S(stream);
+  SIPG_CHECK(launch_setup(h, s), "setup");
+  int status = 0;
+  SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_scratch_setup, sizeof(int), cudaMemcpyDeviceToHost, s),
+             "setup status");
+  SIPG_CHECK(cudaStreamSynchronize(s), "setup sync");
+  if (status != 0) {
+    h->bound = false;
+    return fail(h, SIPG_EINVAL, "setup: a mass matrix was not positive definite");
+  }
+  return SIPG_OK;
+}
+
+sipg_status sipg_rhs(sipg_handle* h, const double* f, double* b, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!f || !b) return fail(h, SIPG_EINVAL, "null vector");
+  SIPG_CHECK(launch_mass(h, f, b, S(stream)), "mass");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_manufactured_source(sipg_handle* h, double* f, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!f) return fail(h, SIPG_EINVAL, "null vector");
+  SIPG_CHECK(launch_manufactured(h, f, S(stream)), "manufactured");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+static sipg_status check_level_prec(sipg_handle* h, int level, int prec) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (level < 0 || level > h->L) return fail(h, SIPG_EINVAL, "level out of range");
+  if (prec != SIPG_FP64 && prec != SIPG_FP32) return fail(h, SIPG_EINVAL, "bad precision");
+  return SIPG_OK;
+}
+
+sipg_status sipg_apply(sipg_handle* h, int level, int prec, const void* x, void* y, void* stream) {
+  sipg_status st = check_level_prec(h, level, prec);
+  if (st) return st;
+  if (!x || !y || x == y) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  cudaError_t e = prec == SIPG_FP64
+                      ? launch_apply<double>(h, level, APPLY_Y, nullptr, (const double*)x, (double*)y, S(stream))
+                      : launch_apply<float>(h, level, APPLY_Y, nullptr, (const float*)x, (float*)y, S(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "apply");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_residual(sipg_handle* h, int level, int prec, const void* b, const void* x, void* r,
+                          void* stream) {
+  sipg_status st = check_level_prec(h, level, prec);
+  if (st) return st;
+  if (!b || !x || !r || x == r) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  cudaError_t e = prec == SIPG_FP64
+                      ? launch_apply<double>(h, level, APPLY_RESIDUAL, (const double*)b, (const double*)x,
+                                             (double*)r, S(stream))
+                      : launch_apply<float>(h, level, APPLY_RESIDUAL, (const float*)b, (const float*)x,
+                                            (float*)r, S(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "residual");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_apply_penalty(sipg_handle* h, const double* x, double* y, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!x || !y || x == y) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_PENALTY, nullptr, x, y, S(stream)), "apply penalty");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_smooth_colour(sipg_handle* h, int level, int prec, int colour, const void* b, void* x,
+                               void* stream) {
+  sipg_status st = check_level_prec(h, level, prec);
+  if (st) return st;
+  if (colour < 0 || colour >= (1 << h->prm.dim)) return fail(h, SIPG_EINVAL, "bad colour");
+  if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  cudaError_t e = prec == SIPG_FP64
+                      ? launch_smooth_colour<double>(h, level, colour, (const double*)b, (double*)x, S(stream))
+                      : launch_smooth_colour<float>(h, level, colour, (const float*)b, (float*)x, S(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "smoother");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_smooth(sipg_handle* h, int level, int prec, int reverse, const void* b, void* x,
+                        void* stream) {
+  sipg_status st = check_level_prec(h, level, prec);
+  if (st) return st;
+  if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  if (prec == SIPG_FP64) return smooth_T<double>(h, level, reverse, (const double*)b, (double*)x, S(stream));
+  return smooth_T<float>(h, level, reverse, (const float*)b, (float*)x, S(stream));
+}
+
+sipg_status sipg_restrict(sipg_handle* h, int fine_level, int prec, const void* rf, void* rc, void* stream) {
+  sipg_status st = check_level_prec(h, fine_level, prec);
+  if (st) return st;
+  if (fine_level < 1) return fail(h, SIPG_EINVAL, "fine_level must be >= 1");
+  if (!rf || !rc) return fail(h, SIPG_EINVAL, "null vector");
+  cudaError_t e = prec == SIPG_FP64
+                      ? launch_restrict<double>(h, fine_level, (const double*)rf, (double*)rc, S(stream))
+                      : launch_restrict<float>(h, fine_level, (const float*)rf, (float*)rc, S(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "restrict");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_prolongate_add(sipg_handle* h, int fine_level, int prec, const void* ec, void* xf,
+                                void* stream) {
+  sipg_status st = check_level_prec(h, fine_level, prec);
+  if (st) return st;
+  if (fine_level < 1) return fail(h, SIPG_EINVAL, "fine_level must be >= 1");
+  if (!ec || !xf) return fail(h, SIPG_EINVAL, "null vector");
+  cudaError_t e = prec == SIPG_FP64
+                      ? launch_prolongate_add<double>(h, fine_level, (const double*)ec, (double*)xf, S(stream))
+                      : launch_prolongate_add<float>(h, fine_level, (const float*)ec, (float*)xf, S(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "prolongate");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_coarse_solve(sipg_handle* h, int prec, const void* b0, void* x0, void* stream) {
+  sipg_status st = check_level_prec(h, 0, prec);
+  if (st) return st;
+  if (!b0 || !x0) return fail(h, SIPG_EINVAL, "null vector");
+  cudaError_t e = prec == SIPG_FP64
+                      ? launch_coarse_solve<double>(h, (const double*)b0, (double*)x0, S(stream))
+                      : launch_coarse_solve<float>(h, (const float*)b0, (float*)x0, S(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "coarse solve");
+  h->launches += 1;
+  return SIPG_OK;
+}
+
+sipg_status sipg_vcycle(sipg_handle* h, int prec, const void* b, void* x, void* stream) {
+  sipg_status st = check_level_prec(h, h->L, prec);
+  if (st) return st;
+  if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  if (prec == SIPG_FP64) return vcycle_T<double>(h, (const double*)b, (double*)x, S(stream));
+  return vcycle_T<float>(h, (const float*)b, (float*)x, S(stream));
+}
+
+sipg_status sipg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit, sipg_info* info,
+                       void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  if (!(rtol > 0.0) || maxit < 0) return fail(h, SIPG_EINVAL, "bad rtol or maxit");
+  return fcg_solve(h, b, x, rtol, maxit, info, S(stream));
+}
+
+sipg_status sipg_adjoint_solve(sipg_handle* h, const double* g, double* lambda, double rtol, int maxit,
+                               sipg_info* info, void* stream) {
+  // A is symmetric (Sec. 2, Eq. bilinear_form), so A^T lambda = g is the
+  // same system.
+  return sipg_solve(h, g, lambda, rtol, maxit, info, stream);
+}
+
+sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host, double rtol, int maxit,
+                            sipg_info* info, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!f_host || !u_host) return fail(h, SIPG_EINVAL, "null host buffer");
+  cudaStream_t s = S(stream);
+  const size_t bytes = h->lv[h->L].ndofs * h->prm.nrhs * sizeof(double);
+  double* db = reinterpret_cast<double*>(h->ws + h->off_hb);
+  double* dx = reinterpret_cast<double*>(h->ws + h->off_hx);
+  SIPG_CHECK(cudaMemcpyAsync(dx, f_host, bytes, cudaMemcpyHostToDevice, s), "H2D");
+  SIPG_CHECK(launch_mass(h, dx, db, s), "mass");
+  h->launches += 1;
+  SIPG_CHECK(cudaMemsetAsync(dx, 0, bytes, s), "memset");
+  sipg_status r = fcg_solve(h, db, dx, rtol, maxit, info, s);
+  if (r != SIPG_OK && r != SIPG_ENOCONV) return r;
+  SIPG_CHECK(cudaMemcpyAsync(u_host, dx, bytes, cudaMemcpyDeviceToHost, s), "D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  return r;
+}
+
+sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* out, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!a || !b || !out) return fail(h, SIPG_EINVAL, "null vector");
+  SIPG_CHECK(launch_dot(h, a, b, out, S(stream)), "dot");
+  return SIPG_OK;
+}
+
+sipg_status sipg_get_constants(sipg_handle* h, int level, int which, int type, double* host_out, int cap,
+                               int* count, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (level < 0 || level > h->L || !host_out || !count || type < 0 || type > 3)
+    return fail(h, SIPG_EINVAL, "bad argument");
+  LevelConst<double> c;
+  cudaStream_t s = S(stream);
+  SIPG_CHECK(cudaMemcpyAsync(&c, h->c64(level), sizeof(c), cudaMemcpyDeviceToHost, s), "D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  const int n = h->n;
+  std::vector<double> v;
+  switch (which) {
+    case 0:
+      for (int t = 0; t < 3; ++t)
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) v.push_back(c.Lself[t][i][j]);
+      break;
+    case 1:
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          v.push_back((i == 0 ? c.alo[j] : 0.0) + (j == n - 1 ? c.glo[i] : 0.0));
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          v.push_back((i == n - 1 ? c.ahi[j] : 0.0) + (j == 0 ? c.ghi[i] : 0.0));
+      break;
+    case 2:
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) v.push_back(c.M[i][j]);
+      break;
+    case 3:
+      for (int i = 0; i < c.p[type]; ++i)
+        for (int j = 0; j < c.p[type]; ++j) v.push_back(c.S[type][i][j]);
+      break;
+    case 4:
+      for (int i = 0; i < c.p[type]; ++i) v.push_back(c.lam[type][i]);
+      break;
+    case 5:
+      for (int o = 0; o < 2; ++o)
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) v.push_back(c.Pc[o][i][j]);
+      break;
+    case 6:
+      for (int i = 0; i < c.m0; ++i)
+        for (int j = 0; j < c.m0; ++j) v.push_back(c.S0[i][j]);
+      break;
+    case 7:
+      for (int i = 0; i < c.m0; ++i) v.push_back(c.lam0[i]);
+      break;
+    case 8:
+      for (int i = 0; i < n; ++i) v.push_back(c.nodes[i]);
+      break;
+    default:
+      return fail(h, SIPG_EINVAL, "bad 'which'");
+  }
+  int cnt = std::min((int)v.size(), cap);
+  for (int i = 0; i < cnt; ++i) host_out[i] = v[i];
+  *count = (int)v.size();
+  return SIPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,282 @@
+// FP64 vector kernels of the outer flexible CG: dot products with a
+// deterministic two-stage reduction (warp shuffles inside a block, fixed-order
+// sum of the per-block partials in a second kernel), device-resident Krylov
+// scalars so that one iteration can be replayed as a CUDA graph without host
+// round trips, and fused updates (x += alpha p, r -= alpha q, ||r||^2 and the
+// FP64 -> FP32 conversion at V-cycle entry; the FP32 -> FP64 conversion of the
+// V-cycle output fused with <r, z> and <z, q>).  Mixed precision: Sec. 5.2.
+#include <math.h>
+
+#include "sipg_internal.cuh"
+
+namespace {
+
+constexpr int RB = 256;  // threads per reduction block
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of up to 3 values, fixed order; result valid in thread 0.
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&v)[NQ]) {
+  __shared__ double red[NQ][RB / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double s = warp_sum(v[q]);
+    if (lane == 0) red[q][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = (lane < RB / 32) ? red[q][lane] : 0.0;
+      v[q] = warp_sum(s);
+    }
+  }
+}
+
+struct DotArgs {
+  const double* a[3];
+  const double* b[3];
+};
+
+template <int NQ>
+__global__ void __launch_bounds__(RB) dot_partial_kernel(DotArgs args, long long n, double* partials) {
+  const long long col = (long long)blockIdx.y * n;
+  double v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = fma(args.a[q][col + i], args.b[q][col + i], v[q]);
+  }
+  block_sum<NQ>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) partials[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 3 + q] = v[q];
+  }
+}
+
+enum { FIN_INIT = 0, FIN_RHO_FIRST, FIN_RHO_NEXT, FIN_PQ, FIN_RR, FIN_OUT };
+
+// One block per column: sums the nb partials of each quantity in a fixed
+// order and updates the Krylov scalars of that column.
+__global__ void __launch_bounds__(RB) finalize_kernel(int mode, KrylovScalars* sc, const double* partials,
+                                                      int nb, double rtol2, double* out) {
+  const int col = blockIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < nb; i += RB) {
+    const double* p = partials + ((long long)col * nb + i) * 3;
+    v[0] += p[0];
+    v[1] += p[1];
+    v[2] += p[2];
+  }
+  block_sum<3>(v);
+  if (threadIdx.x != 0) return;
+  KrylovScalars& s = sc[col];
+  switch (mode) {
+    case FIN_INIT:
+      s.bb = v[0];
+      s.rr = v[1];
+      s.rho = s.alpha = s.beta = s.pq = s.zq = 0.0;
+      s.breakdown = !(isfinite(v[0]) && isfinite(v[1]));
+      s.active = (!s.breakdown && v[0] > 0.0 && v[1] > rtol2 * v[0]) ? 1 : 0;
+      break;
+    case FIN_RHO_FIRST:
+      s.rho = v[0];
+      if (s.active && !isfinite(v[0])) {
+        s.breakdown = 1;
+        s.active = 0;
+      }
+      break;
+    case FIN_RHO_NEXT: {
+      // flexible CG: beta = <z_{i+1}, r_{i+1} - r_i> / <z_i, r_i>
+      //                   = -alpha_i <z_{i+1}, q_i> / <z_i, r_i>   (r_{i+1} = r_i - alpha_i q_i)
+      double beta = 0.0;
+      if (s.active) {
+        beta = -s.alpha * v[1] / s.rho;
+        if (!isfinite(beta) || !isfinite(v[0])) {
+          s.breakdown = 1;
+          s.active = 0;
+          beta = 0.0;
+        }
+      }
+      s.beta = beta;
+      s.zq = v[1];
+      s.rho = v[0];
+      break;
+    }
+    case FIN_PQ: {
+      s.pq = v[0];
+      double alpha = 0.0;
+      if (s.active) {
+        if (v[0] > 0.0 && isfinite(v[0]) && isfinite(s.rho)) {
+          alpha = s.rho / v[0];
+        } else {
+          s.breakdown = 1;
+          s.active = 0;
+        }
+      }
+      s.alpha = alpha;
+      break;
+    }
+    case FIN_RR:
+      s.rr = v[0];
+      if (s.active && !isfinite(v[0])) {
+        s.breakdown = 1;
+        s.active = 0;
+      } else if (s.active && v[0] <= rtol2 * s.bb) {
+        s.active = 0;
+      }
+      break;
+    case FIN_OUT:
+      out[col] = v[0];
+      break;
+  }
+}
+
+// z = double(zsrc) (if zsrc differs), partial <r, z> and <z, q>.
+template <typename TZ>
+__global__ void __launch_bounds__(RB) precond_post_kernel(const TZ* zsrc, double* z, const double* r,
+                                                          const double* q, long long n, double* partials,
+                                                          int want_zq) {
+  const long long col = (long long)blockIdx.y * n;
+  double v[3] = {0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+    double zi = (double)zsrc[col + i];
+    if ((const void*)zsrc != (const void*)z) z[col + i] = zi;
+    v[0] = fma(r[col + i], zi, v[0]);
+    if (want_zq) v[1] = fma(zi, q[col + i], v[1]);
+  }
+  block_sum<3>(v);
+  if (threadIdx.x == 0) {
+    double* p = partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 3;
+    p[0] = v[0];
+    p[1] = v[1];
+    p[2] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(RB) p_update_kernel(int first, const double* z, double* p,
+                                                      const KrylovScalars* sc, long long n) {
+  const long long col = (long long)blockIdx.y * n;
+  const double beta = first ? 0.0 : sc[blockIdx.y].beta;
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride)
+    p[col + i] = first ? z[col + i] : fma(beta, p[col + i], z[col + i]);
+}
+
+// x += alpha p, r -= alpha q, partial ||r||^2, optional V-cycle input bL = r.
+template <typename TB>
+__global__ void __launch_bounds__(RB) xr_update_kernel(double* x, double* r, const double* p, const double* q,
+                                                       const KrylovScalars* sc, TB* bL, long long n,
+                                                       double* partials) {
+  const long long col = (long long)blockIdx.y * n;
+  const double alpha = sc[blockIdx.y].alpha;
+  double v[3] = {0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+    const long long j = col + i;
+    x[j] = fma(alpha, p[j], x[j]);
+    double ri = fma(-alpha, q[j], r[j]);
+    r[j] = ri;
+    v[0] = fma(ri, ri, v[0]);
+    if (bL) bL[j] = (TB)ri;
+  }
+  block_sum<3>(v);
+  if (threadIdx.x == 0) {
+    double* pp = partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 3;
+    pp[0] = v[0];
+    pp[1] = 0.0;
+    pp[2] = 0.0;
+  }
+}
+
+__global__ void d2f_kernel(const double* a, float* b, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (float)a[i];
+}
+__global__ void f2d_kernel(const float* a, double* b, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (double)a[i];
+}
+
+}  // namespace
+
+static inline long long fine_n(const sipg_handle* h) { return (long long)h->lv[h->L].ndofs; }
+
+cudaError_t launch_dot(sipg_handle* h, const double* a, const double* b, double* out,
+                       cudaStream_t s) {
+  DotArgs args{{a, nullptr, nullptr}, {b, nullptr, nullptr}};
+  dim3 grid(h->n_partials, h->prm.nrhs);
+  dot_partial_kernel<1><<<grid, RB, 0, s>>>(args, fine_n(h), h->partials());
+  finalize_kernel<<<h->prm.nrhs, RB, 0, s>>>(FIN_OUT, h->scalars(), h->partials(), h->n_partials,
+                                             0.0, out);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t krylov_init_norms(sipg_handle* h, const double* b, const double* r, cudaStream_t s) {
+  DotArgs args{{b, r, nullptr}, {b, r, nullptr}};
+  dim3 grid(h->n_partials, h->prm.nrhs);
+  dot_partial_kernel<2><<<grid, RB, 0, s>>>(args, fine_n(h), h->partials());
+  finalize_kernel<<<h->prm.nrhs, RB, 0, s>>>(FIN_INIT, h->scalars(), h->partials(), h->n_partials,
+                                             h->rtol2, nullptr);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t krylov_after_precond(sipg_handle* h, int first, const double* r, const void* zsrc,
+                                 int zsrc_is_float, cudaStream_t s) {
+  dim3 grid(h->n_partials, h->prm.nrhs);
+  if (zsrc_is_float)
+    precond_post_kernel<float><<<grid, RB, 0, s>>>((const float*)zsrc, h->kz(), r, h->kq(), fine_n(h),
+                                                   h->partials(), first ? 0 : 1);
+  else
+    precond_post_kernel<double><<<grid, RB, 0, s>>>((const double*)zsrc, h->kz(), r, h->kq(), fine_n(h),
+                                                    h->partials(), first ? 0 : 1);
+  finalize_kernel<<<h->prm.nrhs, RB, 0, s>>>(first ? FIN_RHO_FIRST : FIN_RHO_NEXT, h->scalars(),
+                                             h->partials(), h->n_partials, h->rtol2, nullptr);
+  p_update_kernel<<<grid, RB, 0, s>>>(first, h->kz(), h->kp(), h->scalars(), fine_n(h));
+  h->launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t krylov_after_apply(sipg_handle* h, cudaStream_t s) {
+  DotArgs args{{h->kp(), nullptr, nullptr}, {h->kq(), nullptr, nullptr}};
+  dim3 grid(h->n_partials, h->prm.nrhs);
+  dot_partial_kernel<1><<<grid, RB, 0, s>>>(args, fine_n(h), h->partials());
+  finalize_kernel<<<h->prm.nrhs, RB, 0, s>>>(FIN_PQ, h->scalars(), h->partials(), h->n_partials,
+                                             h->rtol2, nullptr);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t krylov_update_xr(sipg_handle* h, double* x, void* bL, int bL_is_float, cudaStream_t s) {
+  dim3 grid(h->n_partials, h->prm.nrhs);
+  if (bL_is_float)
+    xr_update_kernel<float><<<grid, RB, 0, s>>>(x, h->kr(), h->kp(), h->kq(), h->scalars(), (float*)bL,
+                                                fine_n(h), h->partials());
+  else
+    xr_update_kernel<double><<<grid, RB, 0, s>>>(x, h->kr(), h->kp(), h->kq(), h->scalars(),
+                                                 (double*)bL, fine_n(h), h->partials());
+  finalize_kernel<<<h->prm.nrhs, RB, 0, s>>>(FIN_RR, h->scalars(), h->partials(), h->n_partials,
+                                             h->rtol2, nullptr);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t convert_d2f(const double* a, float* b, size_t n, cudaStream_t s) {
+  d2f_kernel<<<ceil_div((long long)n, 256 * 8), 256, 0, s>>>(a, b, (long long)n);
+  return cudaGetLastError();
+}
+cudaError_t convert_f2d(const float* a, double* b, size_t n, cudaStream_t s) {
+  f2d_kernel<<<ceil_div((long long)n, 256 * 8), 256, 0, s>>>(a, b, (long long)n);
+  return cudaGetLastError();
+}

@@ -1,0 +1,156 @@
+// Internal declarations shared by the CUDA translation units of the SIPG
+// multigrid library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sipg.h"
+
+#define SIPG_MAXN 8    // n = k+1 <= 8
+#define SIPG_MAXP 16   // 1D patch size 2n
+#define SIPG_MAXPE 18  // 2n plus one halo node on each side
+#define SIPG_MAXM0 64  // 1D size of the coarsest level, N_0 * n
+
+// Per-level constants, written by the device setup kernel (FP64) and copied
+// to an FP32 twin.  All 1D operators include kappa; physical cell size h.
+// Index convention: [test row][trial column].
+template <typename T>
+struct LevelConst {
+  int N;      // cells per direction
+  int n;      // nodes per direction per cell (k+1)
+  int m0;     // N * n on the coarsest level, 0 elsewhere
+  int pad_;
+  T h, gamma;
+  // 1D SIPG self block of a cell: stiffness + its two faces.  Type 0: both
+  // faces interior; 1: low face on the boundary; 2: high face on the boundary.
+  T Lself[3][SIPG_MAXN][SIPG_MAXN];
+  // Coupling to the low neighbour (test in c, trial in c-1) is rank two:
+  //   l_lo[i][j] = delta_{i0} alo[j] + delta_{jk} glo[i]
+  // and to the high neighbour (trial in c+1):
+  //   l_hi[i][j] = delta_{ik} ahi[j] + delta_{j0} ghi[i].
+  T alo[SIPG_MAXN], glo[SIPG_MAXN], ahi[SIPG_MAXN], ghi[SIPG_MAXN];
+  // Same objects for dA/dgamma (unit penalty, times kappa).
+  T Pself[3][SIPG_MAXN][SIPG_MAXN];
+  T palo[SIPG_MAXN], pglo[SIPG_MAXN], pahi[SIPG_MAXN], pghi[SIPG_MAXN];
+  T M[SIPG_MAXN][SIPG_MAXN];  // 1D cell mass h * Mhat
+  // Vertex-patch 1D data per type t (bit 0: low end on the domain boundary,
+  // bit 1: high end).  Patch-local 1D node a = o*n + i, o in {0,1}.  V_j keeps
+  // a in [first, first+p).  Lr/Mr are the rows V_j of the 1D patch matrices
+  // over the extended columns (0 = low halo node, 1..2n = patch, 2n+1 = high
+  // halo node); Mr has zero halo columns.
+  int p[4], first[4];
+  T Lr[4][SIPG_MAXP][SIPG_MAXPE];
+  T Mr[4][SIPG_MAXP][SIPG_MAXPE];
+  T S[4][SIPG_MAXP][SIPG_MAXP];  // M-orthonormal generalised eigenvectors (columns)
+  T lam[4][SIPG_MAXP];
+  // Canonical embedding: Pc[o][i][j] = phi_j((o + xi_i) / 2).
+  T Pc[2][SIPG_MAXN][SIPG_MAXN];
+  T nodes[SIPG_MAXN];  // Gauss-Lobatto nodes on [0,1]
+  // Coarsest level only: global 1D eigenpairs L S0 = M S0 Lambda0.
+  T S0[SIPG_MAXM0][SIPG_MAXM0];
+  T lam0[SIPG_MAXM0];
+};
+
+// Per-rhs scalars of the flexible CG (device memory).
+struct KrylovScalars {
+  double rho;      // <r_i, z_i>
+  double alpha;
+  double beta;
+  double pq;       // <p_i, q_i>
+  double rr;       // ||r||^2
+  double bb;       // ||b||^2
+  double zq;       // <z_{i+1}, q_i>
+  int active;      // 1 while this column has not converged
+  int breakdown;   // set when a scalar is non-finite or <p,q> <= 0
+};
+
+struct LevelInfo {
+  int N;
+  size_t ndofs;    // one rhs
+  size_t ncells;
+};
+
+struct sipg_handle {
+  sipg_params prm;
+  int n;           // k+1
+  int L;           // finest level index
+  std::vector<LevelInfo> lv;
+  std::string err;
+  uint64_t launches = 0;
+
+  // workspace layout (byte offsets)
+  size_t ws_bytes = 0;
+  size_t off_const64 = 0, off_const32 = 0, off_scratch_setup = 0;
+  std::vector<size_t> off_b, off_x, off_r;   // level vectors, vcycle precision
+  size_t off_bL = 0, off_xL = 0;             // finest-level V-cycle vectors
+  size_t off_kr = 0, off_kz = 0, off_kp = 0, off_kq = 0;  // Krylov vectors FP64
+  size_t off_hb = 0, off_hx = 0;             // device b and x of sipg_solve_host
+  size_t off_partials = 0, off_scalars = 0;
+  int n_partials = 0;                        // reduction blocks per rhs
+  double rtol2 = 0.0;                        // squared relative tolerance of the running solve
+  size_t vec_elem = 8;                       // bytes per element of level vectors
+
+  char* ws = nullptr;
+  bool bound = false;
+
+  // CUDA graph of one Krylov iteration (optional)
+  cudaGraphExec_t iter_exec = nullptr;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  double* g_x = nullptr;
+  uint64_t graph_launches = 0;               // kernels inside one graph launch
+
+  LevelConst<double>* c64(int l) const { return reinterpret_cast<LevelConst<double>*>(ws + off_const64) + l; }
+  LevelConst<float>* c32(int l) const { return reinterpret_cast<LevelConst<float>*>(ws + off_const32) + l; }
+  template <typename T> LevelConst<T>* cst(int l) const;
+  void* vb(int l) const { return ws + off_b[l]; }
+  void* vx(int l) const { return ws + off_x[l]; }
+  void* vr(int l) const { return ws + off_r[l]; }
+  double* kr() const { return reinterpret_cast<double*>(ws + off_kr); }
+  double* kz() const { return reinterpret_cast<double*>(ws + off_kz); }
+  double* kp() const { return reinterpret_cast<double*>(ws + off_kp); }
+  double* kq() const { return reinterpret_cast<double*>(ws + off_kq); }
+  double* partials() const { return reinterpret_cast<double*>(ws + off_partials); }
+  KrylovScalars* scalars() const { return reinterpret_cast<KrylovScalars*>(ws + off_scalars); }
+};
+template <> inline LevelConst<double>* sipg_handle::cst<double>(int l) const { return c64(l); }
+template <> inline LevelConst<float>* sipg_handle::cst<float>(int l) const { return c32(l); }
+
+// ---------------------------------------------------------------- launchers
+// Each returns cudaGetLastError() after its launches; `nrhs` columns of
+// length `ndofs` are processed.
+cudaError_t launch_setup(sipg_handle* h, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const sipg_handle* h, int level, int mode, const T* b, const T* x, T* y,
+                         cudaStream_t s);
+cudaError_t launch_mass(const sipg_handle* h, const double* f, double* b, cudaStream_t s);
+cudaError_t launch_manufactured(const sipg_handle* h, double* f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_smooth_colour(const sipg_handle* h, int level, int colour, const T* b, T* x,
+                                 cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(const sipg_handle* h, int fine_level, const T* rf, T* rc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolongate_add(const sipg_handle* h, int fine_level, const T* ec, T* xf,
+                                  cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(const sipg_handle* h, const T* b0, T* x0, cudaStream_t s);
+
+// apply modes
+enum { APPLY_Y = 0, APPLY_RESIDUAL = 1, APPLY_PENALTY = 2 };
+
+// Krylov kernels (krylov.cu)
+cudaError_t launch_dot(sipg_handle* h, const double* a, const double* b, double* out,
+                       cudaStream_t s);
+cudaError_t krylov_init_norms(sipg_handle* h, const double* b, const double* r, cudaStream_t s);
+cudaError_t krylov_after_precond(sipg_handle* h, int first, const double* r, const void* zsrc,
+                                 int zsrc_is_float, cudaStream_t s);
+cudaError_t krylov_after_apply(sipg_handle* h, cudaStream_t s);
+cudaError_t krylov_update_xr(sipg_handle* h, double* x, void* bL, int bL_is_float, cudaStream_t s);
+cudaError_t convert_d2f(const double* a, float* b, size_t n, cudaStream_t s);
+cudaError_t convert_f2d(const float* a, double* b, size_t n, cudaStream_t s);
+cudaError_t copy_or_zero(void* dst, size_t bytes, cudaStream_t s);
+
+static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -1,0 +1,56 @@
+// Small tensor-product building blocks used by the kernels: 1D contractions
+// of an n-point line held in registers against an n x n matrix in shared
+// memory, and index helpers for the cell-wise lexicographic layout
+// (Sec. 4.1: DoF (c, i) at c * n^d + i, i = i0 + n (i1 + n i2)).
+#pragma once
+#include "sipg_internal.cuh"
+
+template <int DIM, int NN>
+struct CellShape {
+  static constexpr int n = NN;
+  static constexpr int lines = (DIM == 2) ? NN : NN * NN;       // lines per direction
+  static constexpr int dofs = (DIM == 2) ? NN * NN : NN * NN * NN;
+  // base offset and stride of line `l` along direction e inside a cell
+  __device__ static inline void line(int e, int l, int& base, int& stride) {
+    if (DIM == 2) {
+      if (e == 0) { base = l * NN; stride = 1; }
+      else { base = l; stride = NN; }
+    } else {
+      if (e == 0) { base = l * NN; stride = 1; }                         // l = iy + n iz
+      else if (e == 1) { base = (l % NN) + (l / NN) * NN * NN; stride = NN; }  // l = ix + n iz
+      else { base = l; stride = NN * NN; }                                // l = ix + n iy
+    }
+  }
+};
+
+// out[i] (+)= sum_j A[i][j] v[j] for a line held in registers.
+template <int NN, typename T>
+__device__ __forceinline__ void matvec_line(const T* __restrict__ A, const T (&v)[NN], T (&o)[NN]) {
+#pragma unroll
+  for (int i = 0; i < NN; ++i) {
+    T s = A[i * NN] * v[0];
+#pragma unroll
+    for (int j = 1; j < NN; ++j) s = fma(A[i * NN + j], v[j], s);
+    o[i] = s;
+  }
+}
+
+template <int NN, typename T>
+__device__ __forceinline__ void load_line(const T* __restrict__ p, int stride, T (&v)[NN]) {
+#pragma unroll
+  for (int j = 0; j < NN; ++j) v[j] = p[j * stride];
+}
+
+template <int NN, typename T>
+__device__ __forceinline__ void store_line(T* __restrict__ p, int stride, const T (&v)[NN]) {
+#pragma unroll
+  for (int j = 0; j < NN; ++j) p[j * stride] = v[j];
+}
+
+// Copy an n x n block stored with leading dimension SIPG_MAXN into a compact
+// n x n shared-memory array.
+template <int NN, typename T>
+__device__ __forceinline__ void copy_block(T* __restrict__ dst, const T (*src)[SIPG_MAXN], int tid,
+                                           int nthreads) {
+  for (int e = tid; e < NN * NN; e += nthreads) dst[e] = src[e / NN][e % NN];
+}

@@ -1,0 +1,335 @@
+"""Element-by-element parity of the CUDA path (through the C ABI) with the
+FP64 CPU oracle on seeded inputs.
+
+Tolerances (derivations in DESIGN.md, "Parity tolerances"):
+  FP64 operator apply / residual / mass / transfer: 1e-12 relative (max norm)
+  FP64 smoother, V-cycle:                           1e-10 relative
+  FP64 solve (rtol 1e-12) vs exact solution:        1e-10 relative
+  FP32 kernels: 64 u_32 |A||x| for the apply; 1e-4 relative for the
+  smoother / V-cycle output (FP32 fast diagonalisation of patch matrices
+  with condition numbers up to ~1e3); mixed solve: 1e-8 relative.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import dev, gpu_available, host, make, rel_inf
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+from oracle.assembly import assemble, rhs_from_nodal  # noqa: E402
+from oracle.basis import gauss_lobatto, lagrange_values  # noqa: E402
+from oracle.direct import GlobalFD, one_d_matrices  # noqa: E402
+from oracle.layout import node_coordinates  # noqa: E402
+from oracle.mg import Hierarchy, Level, mg_solve, prolongation, smooth  # noqa: E402
+from paper_2405_18982_gb300 import SIPG_FP32, SIPG_FP64, inputs  # noqa: E402
+
+# (dim, k, log2 N, levels): 2D and 3D, k = 1..7, several CTAs per launch
+CASES = [(2, 1, 3, 2), (2, 2, 4, 3), (2, 3, 3, 2), (2, 5, 3, 2), (2, 7, 3, 2),
+         (3, 1, 3, 2), (3, 2, 3, 2), (3, 3, 3, 2), (3, 4, 2, 2), (3, 5, 2, 2), (3, 7, 2, 2),
+         (3, 2, 1, 1), (2, 4, 2, 1)]
+IDS = [f"d{d}k{k}N{1 << l}L{n}" for d, k, l, n in CASES]
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_setup_constants(case):
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl, kappa=1.3, eta=1.1)
+    n = k + 1
+    assert np.allclose(s.get_constants(0, 8), gauss_lobatto(k)[0], atol=1e-15, rtol=0)
+    for lev in range(nl):
+        N = (1 << l2) >> (nl - 1 - lev)
+        L1, M1 = one_d_matrices(k, N, 1.3, 1.1)
+        scale = np.abs(L1).max()
+        self_blocks = s.get_constants(lev, 0).reshape(3, n, n)
+        nb = s.get_constants(lev, 1).reshape(2, n, n)
+        assert rel_inf(s.get_constants(lev, 2).reshape(n, n), M1[:n, :n]) < 1e-14
+        assert np.abs(self_blocks[1] - L1[:n, :n]).max() < 1e-13 * scale          # low boundary cell
+        assert np.abs(self_blocks[2] - L1[-n:, -n:]).max() < 1e-13 * scale        # high boundary cell
+        if N >= 3:
+            assert np.abs(self_blocks[0] - L1[n:2 * n, n:2 * n]).max() < 1e-13 * scale
+        assert np.abs(nb[0] - L1[n:2 * n, :n]).max() < 1e-13 * scale            # l_lo: test c, trial c-1
+        assert np.abs(nb[1] - L1[:n, n:2 * n]).max() < 1e-13 * scale            # l_hi
+        # patch eigenpairs: L S = M S Lambda, S^T M S = I on the restricted 1D patch matrices
+        for t in range(4):
+            if (t == 3) != (N == 2):
+                continue
+            if t == 0 and N < 4:
+                continue
+            v = {0: 2, 1: 1, 2: N - 1, 3: 1}[t]
+            start = (v - 1) * n
+            idx = np.arange(start, start + 2 * n)
+            keep = np.ones(2 * n, bool)
+            keep[0] = bool(t & 1)
+            keep[-1] = bool(t & 2)
+            idx = idx[keep]
+            Lp, Mp = L1[np.ix_(idx, idx)], M1[np.ix_(idx, idx)]
+            p = len(idx)
+            S = s.get_constants(lev, 3, t).reshape(p, p)
+            lam = s.get_constants(lev, 4, t)
+            assert np.abs(S.T @ Mp @ S - np.eye(p)).max() < 1e-12
+            assert np.abs(Lp @ S - Mp @ S * lam[None, :]).max() < 1e-11 * np.abs(Lp).max()
+    # coarse level global eigenpairs
+    N0 = (1 << l2) >> (nl - 1)
+    L0, M0 = one_d_matrices(k, N0, 1.3, 1.1)
+    m = N0 * n
+    S0 = s.get_constants(0, 6).reshape(m, m)
+    lam0 = s.get_constants(0, 7)
+    assert np.abs(S0.T @ M0 @ S0 - np.eye(m)).max() < 1e-12
+    assert np.abs(L0 @ S0 - M0 @ S0 * lam0[None, :]).max() < 1e-11 * np.abs(L0).max()
+    # transfer matrices
+    nodes = gauss_lobatto(k)[0]
+    Pc = s.get_constants(0, 5).reshape(2, n, n)
+    for o in range(2):
+        assert np.abs(Pc[o] - lagrange_values(nodes, (o + nodes) / 2)).max() < 1e-14
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_apply_fp64(case):
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl, kappa=0.7, eta=1.2)
+    for lev in range(nl):
+        N = (1 << l2) >> (nl - 1 - lev)
+        A = assemble(dim, k, N, 0.7, 1.2)
+        x = inputs.uniform(100 + lev, A.shape[0])
+        y_ref = A @ x
+        xd = dev(x)
+        yd = dev(np.zeros_like(x))
+        s.apply(lev, xd, yd)
+        assert rel_inf(host(yd), y_ref) < 1e-12
+        b = inputs.uniform(200 + lev, A.shape[0])
+        rd = dev(np.zeros_like(x))
+        s.residual(lev, dev(b), xd, rd)
+        assert rel_inf(host(rd), b - y_ref) < 1e-12
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_apply_fp32(case):
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl)
+    lev = nl - 1
+    N = 1 << l2
+    A = assemble(dim, k, N)
+    x32 = inputs.uniform(300, A.shape[0]).astype(np.float32)
+    y_ref = A @ x32.astype(np.float64)
+    scale = np.abs(abs(A) @ np.abs(x32.astype(np.float64))).max()
+    import torch
+    yd = dev(np.zeros(A.shape[0]), torch.float32)
+    s.apply(lev, dev(x32, torch.float32), yd)
+    assert np.abs(host(yd) - y_ref).max() < 64 * 6e-8 * scale
+
+
+@pytest.mark.parametrize("case", CASES[:6], ids=IDS[:6])
+def test_apply_penalty_and_mass(case):
+    dim, k, l2, nl = case
+    N = 1 << l2
+    s = make(dim, k, l2, nl, kappa=1.4)
+    x = inputs.normal(400, s.ndofs())
+    Ap = assemble(dim, k, N, 1.4, 1.0, part="penalty")
+    yd = dev(np.zeros_like(x))
+    s.apply_penalty(dev(x), yd)
+    assert rel_inf(host(yd), Ap @ x) < 1e-12
+    bd = dev(np.zeros_like(x))
+    s.rhs(dev(x), bd)
+    assert rel_inf(host(bd), rhs_from_nodal(dim, k, N, x)) < 1e-13
+
+
+@pytest.mark.parametrize("case", CASES[:6], ids=IDS[:6])
+def test_manufactured_source(case):
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl)
+    fd = dev(np.zeros(s.ndofs()))
+    s.manufactured_source(fd)
+    X = node_coordinates(dim, 1 << l2, gauss_lobatto(k)[0])
+    ref = dim * np.pi ** 2 * np.prod(np.sin(np.pi * X), axis=1)
+    assert np.abs(host(fd) - ref).max() < 1e-13 * dim * np.pi ** 2
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["consistent", "paper"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_smooth_colour_fp64(case, variant):
+    dim, k, l2, nl = case
+    N = 1 << l2
+    s = make(dim, k, l2, nl, kappa=0.9, smoother=variant)
+    lev = Level(dim, k, N, 0.9, 1.0, "consistent" if variant == 0 else "paper")
+    b = inputs.normal(500, lev.ndof)
+    x0 = inputs.normal(501, lev.ndof)
+    bd = dev(b)
+    xd = dev(x0)
+    x = x0.copy()
+    for c in range(2 ** dim):
+        s.smooth_colour(nl - 1, c, bd, xd)
+        x = smooth(lev, x, b, colours=[c])
+        got = host(xd)
+        assert np.abs(got - x).max() <= 1e-10 * max(np.abs(x - x0).max(), 1e-30), f"colour {c}"
+
+
+@pytest.mark.parametrize("case", CASES[:8], ids=IDS[:8])
+def test_smooth_step_reverse(case):
+    dim, k, l2, nl = case
+    N = 1 << l2
+    s = make(dim, k, l2, nl)
+    lev = Level(dim, k, N)
+    b = inputs.normal(510, lev.ndof)
+    xd = dev(np.zeros(lev.ndof))
+    s.smooth(nl - 1, dev(b), xd, reverse=True)
+    ref = smooth(lev, np.zeros(lev.ndof), b, reverse=True)
+    assert rel_inf(host(xd), ref) < 1e-10
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[3] > 1], ids=[i for c, i in zip(CASES, IDS) if c[3] > 1])
+def test_transfer(case):
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl)
+    for fl in range(1, nl):
+        Nc = (1 << l2) >> (nl - fl)
+        P = prolongation(dim, k, Nc)
+        rf = inputs.normal(600 + fl, P.shape[0])
+        rc = dev(np.zeros(P.shape[1]))
+        s.restrict(fl, dev(rf), rc)
+        assert rel_inf(host(rc), P.T @ rf) < 1e-13
+        ec = inputs.normal(610 + fl, P.shape[1])
+        xf0 = inputs.normal(620 + fl, P.shape[0])
+        xf = dev(xf0)
+        s.prolongate_add(fl, dev(ec), xf)
+        assert rel_inf(host(xf), xf0 + P @ ec) < 1e-13
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_coarse_solve(case):
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl, kappa=1.7)
+    N0 = (1 << l2) >> (nl - 1)
+    A0 = assemble(dim, k, N0, 1.7).toarray()
+    b0 = inputs.normal(700, A0.shape[0])
+    xd = dev(np.zeros_like(b0))
+    s.coarse_solve(dev(b0), xd)
+    assert rel_inf(host(xd), np.linalg.solve(A0, b0)) < 1e-11
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_vcycle_fp64(case):
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl, kappa=1.1)
+    H = Hierarchy(dim, k, 1 << l2, nl, 1.1)
+    b = inputs.normal(800, H.A.shape[0])
+    xd = dev(np.zeros_like(b))
+    s.vcycle(dev(b), xd)
+    assert rel_inf(host(xd), H.vcycle(b)) < 1e-10
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_vcycle_fp32(case):
+    import torch
+    dim, k, l2, nl = case
+    s = make(dim, k, l2, nl, prec=SIPG_FP32)
+    H = Hierarchy(dim, k, 1 << l2, nl)
+    b32 = inputs.normal(810, H.A.shape[0]).astype(np.float32)
+    xd = dev(np.zeros(len(b32)), torch.float32)
+    s.vcycle(dev(b32, torch.float32), xd)
+    assert rel_inf(host(xd), H.vcycle(b32.astype(np.float64))) < 1e-4
+
+
+@pytest.mark.parametrize("prec", [SIPG_FP64, SIPG_FP32], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_solve_matches_exact(case, prec):
+    dim, k, l2, nl = case
+    N = 1 << l2
+    s = make(dim, k, l2, nl, prec=prec, kappa=0.8)
+    f = inputs.normal(900, s.ndofs())
+    b = rhs_from_nodal(dim, k, N, f)
+    xd = dev(np.zeros_like(b))
+    info = s.solve(dev(b), xd, rtol=1e-12, maxit=100)
+    u = GlobalFD(dim, k, N, 0.8).solve(b)
+    tol = 1e-10 if prec == SIPG_FP64 else 1e-8
+    assert info.rel_residual <= 1e-12
+    assert rel_inf(host(xd), u) < tol
+
+
+@pytest.mark.parametrize("case", [(2, 2, 4, 3), (3, 2, 3, 2), (3, 3, 3, 2)])
+def test_fcg_history_matches_oracle(case):
+    dim, k, l2, nl = case
+    N = 1 << l2
+    s = make(dim, k, l2, nl)
+    H = Hierarchy(dim, k, N, nl)
+    b = rhs_from_nodal(dim, k, N, inputs.normal(910, H.A.shape[0]))
+    xd = dev(np.zeros_like(b))
+    info = s.solve(dev(b), xd, rtol=1e-10, maxit=100)
+    x_ref, hist = mg_solve(H, b, rtol=1e-10)
+    assert info.iterations == len(hist) - 1
+    h = np.array(info.history[:len(hist)])
+    assert np.allclose(h, hist, rtol=1e-6)
+
+
+def test_multi_rhs_and_graphs():
+    import torch
+    dim, k, l2, nl = 3, 3, 3, 2
+    N = 1 << l2
+    for graphs in (0, 1):
+        s = make(dim, k, l2, nl, prec=SIPG_FP32, nrhs=3, graphs=graphs)
+        n = s.ndofs()
+        F = inputs.normal_columns([920, 921, 922], n)
+        F[2] *= 1e-3                     # columns of very different scale
+        B = np.stack([rhs_from_nodal(dim, k, N, f) for f in F])
+        X = dev(np.zeros_like(B))
+        info = s.solve(dev(B), X, rtol=1e-10, maxit=100)
+        got = host(X)
+        fd = GlobalFD(dim, k, N)
+        for c in range(3):
+            u = fd.solve(B[c])
+            assert rel_inf(got[c], u) < 1e-7
+        assert info.rel_residual <= 1e-10
+        if graphs == 0:
+            ref = got
+        else:
+            assert np.array_equal(got, ref)
+
+
+def test_solve_host_roundtrip():
+    import torch
+    dim, k, l2, nl = 2, 3, 4, 3
+    N = 1 << l2
+    s = make(dim, k, l2, nl, prec=SIPG_FP32)
+    f = inputs.normal(930, s.ndofs())
+    fh = torch.tensor(f, dtype=torch.float64).pin_memory()
+    uh = torch.zeros_like(fh).pin_memory()
+    info = s.solve_host(fh, uh, rtol=1e-12)
+    u = GlobalFD(dim, k, N).solve(rhs_from_nodal(dim, k, N, f))
+    assert rel_inf(uh.numpy(), u) < 1e-8
+
+
+def test_dot_and_edge_cases():
+    import torch
+    from paper_2405_18982_gb300 import SipgError
+    s = make(2, 2, 3, 2, nrhs=2)
+    n = s.ndofs()
+    a = inputs.normal_columns([940, 941], n)
+    b = inputs.normal_columns([942, 943], n)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    s.dot(dev(a), dev(b), out)
+    assert np.allclose(host(out), np.einsum("ij,ij->i", a, b), rtol=1e-13)
+    # maxit exhausted -> ENOCONV reported, not raised when allowed
+    bb = dev(a)
+    x = dev(np.zeros_like(a))
+    info = s.solve(bb, x, rtol=1e-14, maxit=1, allow_noconv=True)
+    assert info.status == -4 and info.iterations == 1
+    # non-finite input -> a clean status, never a crash
+    bad = a.copy()
+    bad[0, 3] = np.nan
+    x.zero_()
+    with pytest.raises(SipgError):
+        s.solve(dev(bad), x, rtol=1e-10, maxit=5)
+    # the context is still usable afterwards
+    x.zero_()
+    info = s.solve(bb, x, rtol=1e-10, maxit=50)
+    assert info.status == 0
+
+
+def test_single_level_is_direct():
+    s = make(3, 3, 1, 1)
+    A = assemble(3, 3, 2)
+    b = inputs.normal(950, A.shape[0])
+    xd = dev(np.zeros_like(b))
+    info = s.solve(dev(b), xd, rtol=1e-12)
+    assert info.iterations == 1
+    assert rel_inf(host(xd), np.linalg.solve(A.toarray(), b)) < 1e-11
