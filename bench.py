@@ -1,0 +1,490 @@
+#!/usr/bin/env python
+"""Benchmark: MDoF/s per V-cycle and time to 1e-10 relative residual, mixed
+precision (FP32 V-cycle inside FP64 flexible CG) vs plain FP64, on one GB300.
+
+Workload: 3D SIPG Poisson on the unit cube, 64^3 cells, 6 levels, Q3
+(16,777,216 DoFs), penalty 2 k(k+1)/h, source f = 3 pi^2 prod sin(pi x_e) at
+the nodes plus seeded U[-1,1] noise per DoF (seed 2), b = M_h f, solved from
+x = 0 to ||r||/||b|| <= 1e-10.
+
+One step = one complete mixed-precision solve (every kernel of the hot path:
+operator apply, colour-pass smoother, restriction, prolongation, coarse solve,
+FP64 Krylov vector kernels).  value = DoFs x V-cycles / time, summed over
+ranks (each rank solves its own replica: the path is not sharded, so N > 1
+runs independent replicas, weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload.
+"""
+import os
+
+# the oracle legs run single-threaded; set before numpy is first imported
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MDoF/s per V-cycle & time to 1e-10 rel. residual, mixed vs FP64 on 1 GB300"
+DIM, K, LOG2N, NLEV = 3, 3, 6, 6
+RTOL = 1e-10
+NOISE_SEED = 2
+WORKLOAD = ("3D SIPG Poisson, unit cube, 64^3 cells, 6 levels, Q3 GLL (16.8M DoFs), "
+            "gamma = 2k(k+1)/h, f = manufactured 3pi^2 prod sin + U[-1,1] noise (seed 2), "
+            "FP32 V-cycle (1+1 vertex-patch smoothing) inside FP64 flexible CG to 1e-10; "
+            "plain FP64 solve timed beside it")
+# peaks (MEASURED_PEAKS.json for HBM; ALU peaks from unit counts x max SM clock)
+SMS, FP32_LANES, FP64_UNITS, SM_MAX_MHZ = 152, 128, 2, 2070.0
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def fp64_peak_tflops(mhz=SM_MAX_MHZ):
+    return SMS * FP64_UNITS * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- algorithmic counts
+def smoother_counts(dim, k, N, colour, s_bytes):
+    """Algorithmic flops and HBM bytes of one colour pass (Algorithm 1 with
+    fast diagonalisation), interior-patch formulas: residual
+    4pP^3 + 6p^2P^2 + 4p^3P, FD 4d p^(d+1) + p^d (P = 2(k+1), p = 2k);
+    bytes = read x on the patch cells, read b and read-modify-write x on V_j."""
+    n = k + 1
+    P, p = 2 * n, 2 * k
+    npatch = 1
+    for e in range(dim):
+        npatch *= N // 2 if (colour >> e) & 1 else N // 2 - 1
+    if dim == 3:
+        fl = 4 * p * P ** 3 + 6 * p * p * P * P + 4 * p ** 3 * P + 4 * dim * p ** (dim + 1) + p ** dim
+        by = (P ** 3 + 3 * p ** 3) * s_bytes
+    else:
+        fl = 4 * p * P * P + 4 * p * p * P + 4 * dim * p ** (dim + 1) + p ** dim
+        by = (P ** 2 + 3 * p ** 2) * s_bytes
+    return npatch * fl, npatch * by, npatch
+
+
+def apply_counts(dim, k, N, s_bytes):
+    """Apply: 3 normal contractions with rank-2 neighbour terms + 5 (3D) mass
+    contractions per DoF; bytes = read x + write y."""
+    n = k + 1
+    nd = N ** dim * n ** dim
+    per = (8 * 2 * n + 2 * dim * 4) if dim == 3 else (4 * 2 * n + 2 * dim * 4)
+    return nd * per, nd * 2 * s_bytes
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2405_18982_gb300 as pkg
+    from paper_2405_18982_gb300 import SIPG, SIPG_FP32, SIPG_FP64, Params, inputs
+    pkg.load(pkg.build())
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    mk = lambda prec: SIPG(Params(dim=DIM, degree=K, log2_cells=LOG2N, n_levels=NLEV,
+                                  vcycle_precision=prec, use_graphs=1), device=dev)
+    s_mix = mk(SIPG_FP32)
+    s_64 = mk(SIPG_FP64)
+    n = s_mix.ndofs()
+    f = torch.zeros(1, n, dtype=torch.float64, device=dev)
+    s_mix.manufactured_source(f)
+    f += torch.from_numpy(inputs.uniform(NOISE_SEED, n)).to(dev).view(1, n)
+    b = torch.zeros_like(f)
+    s_mix.rhs(f, b)
+    x = torch.zeros_like(f)
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- warm-up (also captures the CUDA graphs)
+    for _ in range(args.warmup):
+        x.zero_()
+        s_mix.solve(b, x, rtol=RTOL, maxit=200)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K mixed-precision solves
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = s_mix.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        x.zero_()
+        info = s_mix.solve(b, x, rtol=RTOL, maxit=200)
+        iters.append(info.iterations)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t_mix = ev0.elapsed_time(ev1) / 1e3
+    launches = s_mix.launch_count() - l0 + args.steps  # + the torch zero_ per step
+    t_mix_max = max_over_ranks(t_mix)
+    total_vc = sum_over_ranks(float(sum(iters)))
+    value = n * total_vc / t_mix_max / 1e6
+    rel_res_mix = info.rel_residual
+
+    # solution error of the mixed solve against the FP64 solve (reported)
+    x64 = torch.zeros_like(f)
+    for _ in range(max(1, min(2, args.warmup))):
+        x64.zero_()
+        s_64.solve(b, x64, rtol=RTOL, maxit=200)
+    torch.cuda.synchronize()
+    k64 = max(1, (args.steps + 1) // 2)
+    ev0.record(stream)
+    it64 = []
+    for _ in range(k64):
+        x64.zero_()
+        i64 = s_64.solve(b, x64, rtol=RTOL, maxit=200)
+        it64.append(i64.iterations)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_64 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    err_mix = float(((x - x64).norm() / x64.norm()).item())
+
+    # ---- V-cycle-only throughput (mixed and FP64)
+    bf = b.float()
+    xf = torch.zeros_like(bf)
+    xd = torch.zeros_like(b)
+    for _ in range(2):
+        s_mix.vcycle(bf, xf)
+        s_64.vcycle(b, xd)
+    torch.cuda.synchronize()
+    nv = 10
+    ev0.record(stream)
+    for _ in range(nv):
+        s_mix.vcycle(bf, xf)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_vc32 = ev0.elapsed_time(ev1) / 1e3 / nv
+    ev0.record(stream)
+    for _ in range(3):
+        s_64.vcycle(b, xd)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_vc64 = ev0.elapsed_time(ev1) / 1e3 / 3
+
+    # ---- dominant kernel: finest-level FP32 colour pass, timed per launch
+    L = NLEV - 1
+    N = 1 << LOG2N
+    nrep = 5
+    col_t = []
+    for c in range(2 ** DIM):
+        s_mix.smooth_colour(L, c, bf, xf)
+    torch.cuda.synchronize()
+    tot_fl = tot_by = 0
+    ev0.record(stream)
+    for _ in range(nrep):
+        for c in range(2 ** DIM):
+            s_mix.smooth_colour(L, c, bf, xf)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_col = ev0.elapsed_time(ev1) / 1e3 / (nrep * 2 ** DIM)
+    for c in range(2 ** DIM):
+        fl, by, _ = smoother_counts(DIM, K, N, c, 4)
+        tot_fl += fl
+        tot_by += by
+    fl_launch = tot_fl / 2 ** DIM
+    by_launch = tot_by / 2 ** DIM
+    hbm, hbm_src = measured_peaks()
+    achieved_tf = fl_launch / t_col / 1e12
+    achieved_gb = by_launch / t_col / 1e9
+    peak_tf = fp32_peak_tflops()
+    frac_alu = achieved_tf / peak_tf
+    frac_hbm = achieved_gb / hbm
+    if fl_launch / (peak_tf * 1e12) >= by_launch / (hbm * 1e9):
+        roof = {"bound": "alu", "achieved": round(achieved_tf, 3), "peak": round(peak_tf, 2),
+                "unit": "TFLOP/s", "frac": round(frac_alu, 4),
+                "peak_source": "FP32: 152 SMs x 128 lanes x 2 x 2070 MHz (unit counts x max clock)"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(achieved_gb, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(frac_hbm, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
+    roof.update({"kernel": "smooth_colour_kernel<3,4,float> (finest level, one colour pass)",
+                 "traffic": None, "avg_launch_us": round(t_col * 1e6, 2),
+                 "algorithmic_flops_per_launch": int(fl_launch), "algorithmic_bytes_per_launch": int(by_launch),
+                 "hbm_frac": round(frac_hbm, 4), "alu_frac": round(frac_alu, 4)})
+
+    # ---- end to end through the public host-buffer call
+    fh = f.detach().cpu().pin_memory()
+    uh = torch.zeros_like(fh).pin_memory()
+    s_mix.solve_host(fh, uh, rtol=RTOL)
+    torch.cuda.synchronize()
+    ke = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    it_e = 0
+    for _ in range(ke):
+        ie = s_mix.solve_host(fh, uh, rtol=RTOL)
+        it_e += ie.iterations
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = n * sum_over_ranks(float(it_e)) / t_e2e / 1e6
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MDoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_mix_max / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": DIM, "degree": K, "cells_per_dir": N,
+                       "levels": NLEV, "dofs_per_gpu": n, "rtol": RTOL,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (each FP64 vector 134 MB > 129 MB L2)"},
+            "extra": {
+                "time_to_rtol_s": {"mixed": round(t_mix_max / args.steps, 4), "fp64": round(t_64 / k64, 4)},
+                "speedup_mixed_vs_fp64": round((t_64 / k64) / (t_mix_max / args.steps), 3),
+                "iterations": {"mixed": iters, "fp64": it64},
+                "rel_residual": {"mixed": rel_res_mix, "fp64": i64.rel_residual},
+                "nu": {"mixed": info.nu, "fp64": i64.nu},
+                "mixed_vs_fp64_solution_rel_l2": err_mix,
+                "vcycle_only_mdofs": {"fp32": round(n / t_vc32 / 1e6, 1), "fp64": round(n / t_vc64 / 1e6, 1)},
+                "vcycle_ms": {"fp32": round(t_vc32 * 1e3, 3), "fp64": round(t_vc64 * 1e3, 3)},
+                "fp64_mdofs_per_vcycle_in_solve": round(n * sum(it64) / t_64 / 1e6, 2),
+            },
+            "roofline": roof,
+            "e2e": {"value": round(e2e_value, 2), "unit": "MDoF/s", "h2d_bytes_per_step": n * 8,
+                    "d2h_bytes_per_step": n * 8,
+                    "note": "sipg_solve_host: pinned f in, b = M f, solve from 0, u out"},
+            "clocks": clk,
+            "gpu_launches": int(launches),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- kernel-only runs
+def run_kernel_only(args):
+    """Small-footprint run of one kernel family on the benchmark workload (for
+    profiler captures): --mode smooth (FP32/FP64 finest-level colour passes),
+    apply (FP64/FP32 finest-level operator apply) or vcycle."""
+    import torch
+    import paper_2405_18982_gb300 as pkg
+    from paper_2405_18982_gb300 import SIPG, SIPG_FP32, SIPG_FP64, Params, inputs
+    pkg.load(pkg.build())
+    prec = SIPG_FP64 if args.precision == "fp64" else SIPG_FP32
+    dt = torch.float64 if prec == SIPG_FP64 else torch.float32
+    s = SIPG(Params(dim=DIM, degree=K, log2_cells=LOG2N, n_levels=NLEV, vcycle_precision=prec))
+    n = s.ndofs()
+    b = torch.from_numpy(inputs.uniform(NOISE_SEED, n)).to("cuda").view(1, n).to(dt)
+    x = torch.zeros_like(b)
+    L = NLEV - 1
+
+    def one():
+        if args.mode == "smooth":
+            for c in range(2 ** DIM):
+                s.smooth_colour(L, c, b, x)
+        elif args.mode == "apply":
+            s.apply(L, b, x)
+        else:
+            s.vcycle(b, x)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": args.mode, "precision": args.precision, "ms_per_rep": round(ms, 4),
+                      "launches_per_rep": (2 ** DIM if args.mode == "smooth" else 1)}))
+
+
+# ----------------------------------------------------------------- oracle arm
+SAMPLE = (3, 3, 8, 3)   # dim, k, N, levels: the same discretisation on 8^3 cells
+
+
+def _oracle_sample():
+    import numpy as np
+    from oracle.assembly import rhs_from_nodal
+    from oracle.mg import Hierarchy
+    from paper_2405_18982_gb300 import inputs
+    dim, k, N, nl = SAMPLE
+    H = Hierarchy(dim, k, N, nl)
+    nd = H.A.shape[0]
+    from oracle.layout import node_coordinates
+    from oracle.basis import gauss_lobatto
+    X = node_coordinates(dim, N, gauss_lobatto(k)[0])
+    f = dim * np.pi ** 2 * np.prod(np.sin(np.pi * X), axis=1) + inputs.uniform(NOISE_SEED, nd)
+    b = rhs_from_nodal(dim, k, N, f)
+    return H, b
+
+
+def _oracle_iteration(H, r):
+    """One FCG iteration's preconditioner + operator work in the oracle."""
+    z = H.vcycle(r)
+    q = H.A @ z
+    return z, q
+
+
+def cpu_baseline(seconds=12.0):
+    import numpy as np
+    H, b = _oracle_sample()
+    nd = H.A.shape[0]
+    r = b.copy()
+    _oracle_iteration(H, r)
+    t0 = time.perf_counter()
+    cnt = 0
+    while time.perf_counter() - t0 < seconds:
+        z, _ = _oracle_iteration(H, r)
+        cnt += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(nd * cnt / dt / 1e6, 5), "unit": "MDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle V-cycle + CSR apply (one FCG iteration) on the same discretisation at 8^3 cells "
+                      f"({nd} DoFs, 3 levels), {cnt} iterations in {dt:.1f} s, single thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    H, b = _oracle_sample()
+    nd = H.A.shape[0]
+    r = b.copy()
+    for _ in range(args.warmup):
+        _oracle_iteration(H, r)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_iteration(H, r)
+    dt = time.perf_counter() - t0
+    value = nd * args.steps / dt / 1e6
+    out = {"metric": METRIC, "value": round(value, 5), "unit": "MDoF/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample": "8^3 cells, 3 levels (same k, d, penalty, source)"},
+           "cpu_baseline": {"value": round(value, 5), "unit": "MDoF/s", "cores": 1, "kind": "oracle",
+                            "sample": f"one oracle FCG iteration (V-cycle + CSR apply) per step on 8^3 cells ({nd} DoFs)"},
+           "e2e": {"value": round(value, 5), "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--mode", default="solve", choices=["solve", "smooth", "apply", "vcycle"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.mode != "solve":
+        run_kernel_only(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
