@@ -190,6 +190,19 @@ sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host
  * written to device memory. */
 sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* out, void* stream);
 
+/* Same result as sipg_dot, for callers that cannot allocate device memory
+ * (an application whose allocator already holds all of it, or a latency path
+ * where cudaMalloc would synchronise the device): needs a created handle (for
+ * sizes and error messages) but no bound workspace, and allocates nothing.
+ * Its reduction scratch is a fixed 128 KiB device array inside the library
+ * (kept on every GPU that loads it until exit), so at most 64 columns are
+ * supported (nrhs > 64 -> SIPG_EINVAL).  All calls share that array: calls
+ * whose kernels overlap on the GPU race.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make it before any
+ * stream capture.  The paper has no counterpart to this call. */
+sipg_status sipg_dot_noalloc(sipg_handle* h, const double* a, const double* b, double* out,
+                             void* stream);
+
 /* Copy FP64 level constants to host memory for inspection.  which:
  *  0 Lself (3 x n x n), 1 neighbour blocks [l_lo, l_hi] (2 x n x n),
  *  2 cell mass (n x n), 3 patch eigenvectors S of type t (p x p),

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsipg.so")
-SOURCES = ["api.cu", "setup.cu", "apply.cu", "smoother.cu", "transfer.cu", "krylov.cu"]
+SOURCES = ["api.cu", "setup.cu", "apply.cu", "smoother.cu", "transfer.cu", "krylov.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
