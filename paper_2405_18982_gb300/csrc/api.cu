@@ -405,6 +405,14 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
     h->bound = false;
     return fail(h, SIPG_EINVAL, "setup: a mass matrix was not positive definite");
   }
+  const int nl = h->L + 1;
+  h->hc64.resize(nl);
+  h->hc32.resize(nl);
+  SIPG_CHECK(cudaMemcpyAsync(h->hc64.data(), h->c64(0), sizeof(LevelConst<double>) * nl, cudaMemcpyDeviceToHost, s),
+             "constants D2H");
+  SIPG_CHECK(cudaMemcpyAsync(h->hc32.data(), h->c32(0), sizeof(LevelConst<float>) * nl, cudaMemcpyDeviceToHost, s),
+             "constants D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "setup sync");
   return SIPG_OK;
 }
 

@@ -94,6 +94,11 @@ struct sipg_handle {
 
   char* ws = nullptr;
   bool bound = false;
+  // host copies of the device-computed level constants (read back once at
+  // bind time; kernels receive the small 1D operators as launch parameters)
+  std::vector<LevelConst<double>> hc64;
+  std::vector<LevelConst<float>> hc32;
+  template <typename T> const LevelConst<T>& hcst(int l) const;
 
   // CUDA graph of one Krylov iteration (optional)
   cudaGraphExec_t iter_exec = nullptr;
@@ -117,6 +122,8 @@ struct sipg_handle {
 };
 template <> inline LevelConst<double>* sipg_handle::cst<double>(int l) const { return c64(l); }
 template <> inline LevelConst<float>* sipg_handle::cst<float>(int l) const { return c32(l); }
+template <> inline const LevelConst<double>& sipg_handle::hcst<double>(int l) const { return hc64[l]; }
+template <> inline const LevelConst<float>& sipg_handle::hcst<float>(int l) const { return hc32[l]; }
 
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() after its launches; `nrhs` columns of
