@@ -375,6 +375,35 @@ def run_kernel_only(args):
     x = torch.zeros_like(b)
     L = NLEV - 1
 
+    if args.mode == "levels":
+        # per-level cost of the V-cycle pieces (smoothing step, residual,
+        # transfer) on this workload, CUDA events around each call
+        out = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for lev in range(NLEV - 1, 0, -1):
+            nl = s.ndofs(lev)
+            bl = torch.from_numpy(inputs.uniform(NOISE_SEED + lev, nl)).to("cuda").view(1, nl).to(dt)
+            xl = torch.zeros_like(bl)
+            rl = torch.zeros_like(bl)
+            bc = torch.zeros(1, s.ndofs(lev - 1), dtype=dt, device="cuda")
+            row = {}
+            for name, fn in (("smooth_step", lambda: s.smooth(lev, bl, xl)),
+                             ("residual", lambda: s.residual(lev, bl, xl, rl)),
+                             ("restrict", lambda: s.restrict(lev, rl, bc)),
+                             ("prolongate", lambda: s.prolongate_add(lev, bc, xl))):
+                for _ in range(2):
+                    fn()
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(args.steps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                row[name] = round(e0.elapsed_time(e1) / args.steps * 1e3, 2)
+            out[f"N={1 << (LOG2N - (NLEV - 1 - lev))}"] = row
+        print(json.dumps({"mode": "levels", "precision": args.precision, "us_per_call": out}))
+        return
+
     def one():
         if args.mode == "smooth":
             for c in range(2 ** DIM):
@@ -475,7 +504,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "smooth", "apply", "vcycle"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "smooth", "apply", "vcycle", "levels"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":

@@ -203,6 +203,16 @@ sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* o
 sipg_status sipg_dot_noalloc(sipg_handle* h, const double* a, const double* b, double* out,
                              void* stream);
 
+/* Self test of the bounded device-side waits (fused smoothing steps separate
+ * their colours by a grid barrier whose waits give up after about half a
+ * second, set a status word and return, so a stuck barrier is reported as
+ * SIPG_ETIMEOUT instead of hanging the GPU).  Launches two cooperative CTAs
+ * on a barrier that expects `extra` more CTAs: extra = 0 must pass
+ * (SIPG_OK); extra > 0 can never open, so both waits must run out and the
+ * call returns SIPG_ETIMEOUT.  Resets the barrier state.  Synchronises stream.
+ * The paper has no counterpart to this call. */
+sipg_status sipg_selftest_barrier(sipg_handle* h, int extra, void* stream);
+
 /* Copy FP64 level constants to host memory for inspection.  which:
  *  0 Lself (3 x n x n), 1 neighbour blocks [l_lo, l_hi] (2 x n x n),
  *  2 cell mass (n x n), 3 patch eigenvectors S of type t (p x p),

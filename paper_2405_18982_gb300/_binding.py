@@ -73,6 +73,7 @@ SIGNATURES = {
     "sipg_solve_host": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
     "sipg_dot": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_dot_noalloc": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "sipg_selftest_barrier": (_st, [_vp, _i, _vp]),
     "sipg_get_constants": (_st, [_vp, _i, _i, _i, _vp, _i, ctypes.POINTER(_i), _vp]),
 }
 

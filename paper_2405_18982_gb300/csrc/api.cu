@@ -53,12 +53,9 @@ size_t vec_bytes(const sipg_handle* h, int level, size_t elem) {
 // ------------------------------------------------------------------ V-cycle
 template <typename T>
 sipg_status smooth_T(sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s) {
-  const int nc = 1 << h->prm.dim;
-  for (int i = 0; i < nc; ++i) {
-    int c = reverse ? nc - 1 - i : i;
-    SIPG_CHECK(launch_smooth_colour<T>(h, level, c, b, x, s), "smoother");
-    h->launches += 1;
-  }
+  int nl = 0;
+  SIPG_CHECK(launch_smooth_step<T>(h, level, reverse, b, x, s, &nl), "smoother");
+  h->launches += nl;
   return SIPG_OK;
 }
 
@@ -270,6 +267,20 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
     }
     info->history_len = cnt;
   }
+  {
+    // a bounded grid-barrier wait that ran out (fused smoothing steps)
+    int status = 0;
+    SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_sync + 2 * sizeof(unsigned int), sizeof(int),
+                               cudaMemcpyDeviceToHost, s),
+               "status D2H");
+    SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+    if (status != 0) {
+      SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+      h->err = "a bounded grid-barrier wait in the smoother timed out";
+      if (info) info->status = SIPG_ETIMEOUT;
+      return SIPG_ETIMEOUT;
+    }
+  }
   if (result == SIPG_ENOCONV) h->err = "solver reached maxit before rtol";
   if (result == SIPG_EBREAKDOWN) h->err = "Krylov breakdown (non-finite or non-positive scalar)";
   return result;
@@ -333,6 +344,8 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   off += align256(sizeof(double) * 3 * h->n_partials * p->nrhs);
   h->off_scalars = off;
   off += align256(sizeof(KrylovScalars) * p->nrhs);
+  h->off_sync = off;
+  off += 256;
   h->off_kr = off;
   off += vec_bytes(h, L, 8);
   h->off_kz = off;
@@ -396,6 +409,12 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
   h->ws = reinterpret_cast<char*>(dev_ptr);
   h->bound = true;
   cudaStream_t s = S(stream);
+  {
+    int dev = 0;
+    SIPG_CHECK(cudaGetDevice(&dev), "device");
+    SIPG_CHECK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  }
+  SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
   SIPG_CHECK(launch_setup(h, s), "setup");
   int status = 0;
   SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_scratch_setup, sizeof(int), cudaMemcpyDeviceToHost, s),
@@ -589,6 +608,25 @@ sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* o
   if (st) return st;
   if (!a || !b || !out) return fail(h, SIPG_EINVAL, "null vector");
   SIPG_CHECK(launch_dot(h, a, b, out, S(stream)), "dot");
+  return SIPG_OK;
+}
+
+sipg_status sipg_selftest_barrier(sipg_handle* h, int extra, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (extra < 0 || extra > 1024) return fail(h, SIPG_EINVAL, "extra out of range");
+  cudaStream_t s = S(stream);
+  SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+  SIPG_CHECK(launch_barrier_selftest(h, extra, s), "barrier self test");
+  h->launches += 1;
+  int status = 0;
+  SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_sync + 2 * sizeof(unsigned int), sizeof(int),
+                             cudaMemcpyDeviceToHost, s),
+             "status D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  if (status != 0) return fail(h, SIPG_ETIMEOUT, "barrier wait timed out (self test)");
   return SIPG_OK;
 }
 

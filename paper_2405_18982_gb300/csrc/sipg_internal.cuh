@@ -88,12 +88,15 @@ struct sipg_handle {
   size_t off_kr = 0, off_kz = 0, off_kp = 0, off_kq = 0;  // Krylov vectors FP64
   size_t off_hb = 0, off_hx = 0;             // device b and x of sipg_solve_host
   size_t off_partials = 0, off_scalars = 0;
+  size_t off_sync = 0;                       // grid-barrier state [count, generation] + status word
   int n_partials = 0;                        // reduction blocks per rhs
   double rtol2 = 0.0;                        // squared relative tolerance of the running solve
   size_t vec_elem = 8;                       // bytes per element of level vectors
 
   char* ws = nullptr;
   bool bound = false;
+  int num_sms = 0;                           // of the device the workspace lives on
+  bool fuse_small_levels = true;             // one cooperative launch per smoothing step when it fits one wave
   // host copies of the device-computed level constants (read back once at
   // bind time; kernels receive the small 1D operators as launch parameters)
   std::vector<LevelConst<double>> hc64;
@@ -137,6 +140,12 @@ cudaError_t launch_manufactured(const sipg_handle* h, double* f, cudaStream_t s)
 template <typename T>
 cudaError_t launch_smooth_colour(const sipg_handle* h, int level, int colour, const T* b, T* x,
                                  cudaStream_t s);
+// One smoothing step (all colours, reversed order if `reverse`); reports the
+// number of kernels it launched.
+template <typename T>
+cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s,
+                               int* launches);
+cudaError_t launch_barrier_selftest(const sipg_handle* h, int extra, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict(const sipg_handle* h, int fine_level, const T* rf, T* rc, cudaStream_t s);
 template <typename T>

@@ -28,11 +28,13 @@
 // run a padded variant with p = 2n per direction, where the rows outside V_j
 // have zero operators, the eigenvectors are padded by the identity and their
 // residual is zeroed, so the update is exactly the local solve on V_j.
+#include <algorithm>
+
 #include "tensor_ops.cuh"
 
 namespace {
 
-template <int DIM, int NN, bool BND, typename T>
+template <int DIM, int NN, bool BND, typename T, bool WIDE = (sizeof(T) == 4)>
 struct SC {
   static constexpr int P = 2 * NN;                   // patch nodes per direction
   static constexpr int PO = BND ? 2 * NN : 2 * NN - 2;  // rows per direction
@@ -43,7 +45,7 @@ struct SC {
   // counts of every phase (S2: PO (P+2), FD: PO^2), so no lane idles.  FP32
   // (bound by latency): PO^2 threads, one round for the residual and FD
   // phases and more resident warps per SM.
-  static constexpr int TPP = DIM == 3 ? (sizeof(T) == 8 ? 2 * PO : PO * PO) : PO;
+  static constexpr int TPP = DIM == 3 ? (WIDE ? PO * PO : 2 * PO) : PO;
   static constexpr bool WARP_SYNC = (32 % TPP) == 0;  // patches never straddle warps
   // shared memory per patch (elements)
   static constexpr int X_SZ = DIM == 3 ? P * P * SX : P * SX;
@@ -302,24 +304,23 @@ __device__ __forceinline__ void group_sync() {
   else __syncthreads();
 }
 
-template <int DIM, int NN, bool BND, typename T, int PPC>
-__global__ void __launch_bounds__(SC<DIM, NN, BND, T>::TPP * PPC)
-    smooth_fast_kernel(const __grid_constant__ SmoothOps<SC<DIM, NN, BND, T>::PO, SC<DIM, NN, BND, T>::P, T,
-                                                         SC<DIM, NN, BND, T>::NT> ops,
-                       int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
-                       PatchGrid grid) {
+// Operator sets and shared tables of one CTA: the interior path reads the
+// kernel parameters directly (compile-time offsets: constant-bank operands),
+// the boundary path reads its four padded sets from shared memory (runtime
+// type index).
+template <int DIM, int NN, bool BND, typename T>
+__device__ __forceinline__ void smooth_prefix_setup(
+    const SmoothOps<SC<DIM, NN, BND, T>::PO, SC<DIM, NN, BND, T>::P, T, SC<DIM, NN, BND, T>::NT>& ops,
+    unsigned char* prefix) {
   using C = SC<DIM, NN, BND, T>;
-  constexpr int P = C::P, PO = C::PO, OFF = C::OFF, SX = C::SX, SO = C::SO, TPP = C::TPP;
-  using Ops = Ops1D<PO, P, T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* base = reinterpret_cast<T*>(smem_raw + smooth_prefix_bytes<DIM, NN, BND, T>());
-  Ops* sops = reinterpret_cast<Ops*>(smem_raw);  // boundary kernel: operator sets
-  T* dinv = reinterpret_cast<T*>(smem_raw);      // interior kernel: 1 / eigenvalue sums
+  constexpr int PO = C::PO;
+  using Ops = Ops1D<PO, C::P, T>;
   if (BND) {
     const int* src = reinterpret_cast<const int*>(&ops);
-    int* dst = reinterpret_cast<int*>(sops);
+    int* dst = reinterpret_cast<int*>(prefix);
     for (int e = threadIdx.x; e < (int)(sizeof(Ops) * C::NT / sizeof(int)); e += blockDim.x) dst[e] = src[e];
   } else {
+    T* dinv = reinterpret_cast<T*>(prefix);
     constexpr int ND3 = DIM == 3 ? PO * PO * PO : PO * PO;
     for (int e = threadIdx.x; e < ND3; e += blockDim.x) {
       const int r0 = e % PO, r1 = (e / PO) % PO, r2 = e / (PO * PO);
@@ -328,18 +329,28 @@ __global__ void __launch_bounds__(SC<DIM, NN, BND, T>::TPP * PPC)
       dinv[e] = T(1) / ls;
     }
   }
-  __syncthreads();
+}
 
+// Process patches pbase + slot (slot < PPC) of colour `colour`.  Every thread
+// of the CTA must call this (it contains CTA or warp barriers); threads whose
+// slot is >= PPC, or whose patch is past the end, only take part in barriers.
+template <int DIM, int NN, bool BND, typename T, int PPC, bool WIDE = (sizeof(T) == 4)>
+__device__ __forceinline__ void smooth_chunk(
+    const SmoothOps<SC<DIM, NN, BND, T>::PO, SC<DIM, NN, BND, T>::P, T, SC<DIM, NN, BND, T>::NT>& ops,
+    const unsigned char* prefix, T* base, long long pbase, int colour, const T* __restrict__ b, T* x, int N,
+    int consistent, const PatchGrid& grid) {
+  using C = SC<DIM, NN, BND, T, WIDE>;
+  constexpr int P = C::P, PO = C::PO, OFF = C::OFF, SX = C::SX, SO = C::SO, TPP = C::TPP;
+  using Ops = Ops1D<PO, P, T>;
+  const Ops* sops = reinterpret_cast<const Ops*>(prefix);
+  const T* dinv = reinterpret_cast<const T*>(prefix);
   const int tid = threadIdx.x;
   const int lane = tid % TPP;
   const int pl = tid / TPP;  // patch slot in the CTA
-  const long long col = (long long)blockIdx.y * ndofs;
-  b += col;
-  x += col;
 
   const long long npatch = BND ? grid.n_bnd : grid.n_int;
-  const long long pidx = (long long)blockIdx.x * PPC + pl;
-  const bool valid = pidx < npatch;
+  const long long pidx = pbase + pl;
+  const bool valid = pl < PPC && pidx < npatch;
   int m[3] = {0, 0, 0};
   if (valid) patch_index<DIM, BND>(grid, pidx, m);
   int v[3] = {1, 1, 1}, ty[3] = {0, 0, 0};
@@ -348,7 +359,7 @@ __global__ void __launch_bounds__(SC<DIM, NN, BND, T>::TPP * PPC)
     v[e] = par ? 2 * m[e] + 1 : 2 * m[e] + 2;
     ty[e] = BND ? ((v[e] == 1 ? 1 : 0) | (v[e] == N - 1 ? 2 : 0)) : 0;
   }
-  T* sm = base + (size_t)pl * C::PER_PATCH;
+  T* sm = base + (size_t)(pl < PPC ? pl : 0) * C::PER_PATCH;
   T* R1 = sm;                 // tile + halos, later C/D, later FD ping
   T* R2 = sm + C::RA_SZ;      // A/B, later residual and FD pong
   T* R3 = R1;                 // C/D alias the tile (dead after S1)
@@ -679,6 +690,22 @@ __global__ void __launch_bounds__(SC<DIM, NN, BND, T>::TPP * PPC)
   }
 }
 
+// One colour pass over the interior (BND = false) or boundary patches.
+template <int DIM, int NN, bool BND, typename T, int PPC>
+__global__ void __launch_bounds__(SC<DIM, NN, BND, T>::TPP * PPC)
+    smooth_fast_kernel(const __grid_constant__ SmoothOps<SC<DIM, NN, BND, T>::PO, SC<DIM, NN, BND, T>::P, T,
+                                                         SC<DIM, NN, BND, T>::NT> ops,
+                       int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
+                       PatchGrid grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  smooth_prefix_setup<DIM, NN, BND, T>(ops, smem_raw);
+  __syncthreads();
+  T* base = reinterpret_cast<T*>(smem_raw + smooth_prefix_bytes<DIM, NN, BND, T>());
+  const long long col = (long long)blockIdx.y * ndofs;
+  smooth_chunk<DIM, NN, BND, T, PPC>(ops, smem_raw, base, (long long)blockIdx.x * PPC, colour, b + col, x + col,
+                                     N, consistent, grid);
+}
+
 // patches per CTA: as many as fit 112 KB of shared memory and 512 threads,
 // preferring a whole number of warps
 template <int DIM, int NN, bool BND, typename T>
@@ -725,32 +752,194 @@ cudaError_t launch_part(const sipg_handle* h, int level, int colour, const T* b,
   return cudaGetLastError();
 }
 
+PatchGrid make_grid(int dim, int N, int colour);
+
 template <typename T, int DIM, int NN>
 cudaError_t smooth_dispatch2(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s) {
-  const int N = h->lv[level].N;
+  const PatchGrid g = make_grid(DIM, h->lv[level].N, colour);
+  if (g.n_int + g.n_bnd <= 0) return cudaSuccess;  // no patch of this colour (N = 2)
+  cudaError_t e = launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s);
+  if (e != cudaSuccess) return e;
+  return launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, s);
+}
+
+// ------------------------------------------------------------------ fused step
+// All 2^d colours of one smoothing step in one cooperative launch, for levels
+// whose colour passes are latency bound (one wave of CTAs).  Colours are
+// separated by a grid barrier; every wait is bounded: after ~0.5 s the CTA
+// sets *status and returns (the host reports SIPG_ETIMEOUT), so the GPU never
+// hangs.  Loads of x after a barrier see the other CTAs' writes: the waiting
+// thread fences (gpu scope) after the release is observed, then the CTA
+// synchronises.
+struct StepGrids {
+  PatchGrid g[8];
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, unsigned int expected) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int gen = *vgen;
+    int good = 1;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == expected) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == gen) {
+        if (++it > (1LL << 23)) {
+          good = 0;
+          atomicExch(status, 1);
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int DIM, int NN, typename T>
+struct StepCfg {
+  using CI = SC<DIM, NN, false, T, true>;
+  using CB = SC<DIM, NN, true, T, true>;
+  // one patch per CTA: small levels then spread over every SM (an SM's FP64
+  // pipe, and its latency chain, serve one patch instead of a pack)
+  static constexpr int PPC_I = 1;
+  static constexpr int THREADS = CI::TPP > CB::TPP ? CI::TPP : CB::TPP;
+  static constexpr int PPC_B = 1;
+  static constexpr int PRE_I = smooth_prefix_bytes<DIM, NN, false, T>();
+  static constexpr int PRE_B = smooth_prefix_bytes<DIM, NN, true, T>();
+  static constexpr size_t SLOTS_I = (size_t)PPC_I * CI::PER_PATCH * sizeof(T);
+  static constexpr size_t SLOTS_B = (size_t)PPC_B * CB::PER_PATCH * sizeof(T);
+  static constexpr size_t SMEM = PRE_I + PRE_B + (SLOTS_I > SLOTS_B ? SLOTS_I : SLOTS_B);
+};
+
+template <int DIM, int NN, typename T>
+__global__ void __launch_bounds__(StepCfg<DIM, NN, T>::THREADS)
+    smooth_step_kernel(const __grid_constant__ SmoothOps<SC<DIM, NN, false, T>::PO, SC<DIM, NN, false, T>::P, T, 1> opsi,
+                       const __grid_constant__ SmoothOps<SC<DIM, NN, true, T>::PO, SC<DIM, NN, true, T>::P, T, 4> opsb,
+                       int reverse, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs, int nrhs,
+                       StepGrids grids, unsigned int* bar, int* status) {
+  using Cfg = StepCfg<DIM, NN, T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* pre_i = smem_raw;
+  unsigned char* pre_b = smem_raw + Cfg::PRE_I;
+  T* base = reinterpret_cast<T*>(smem_raw + Cfg::PRE_I + Cfg::PRE_B);
+  smooth_prefix_setup<DIM, NN, false, T>(opsi, pre_i);
+  smooth_prefix_setup<DIM, NN, true, T>(opsb, pre_b);
+  __syncthreads();
+  constexpr int nc = 1 << DIM;
+  for (int ci = 0; ci < nc; ++ci) {
+    const int c = reverse ? nc - 1 - ci : ci;
+    const PatchGrid& g = grids.g[c];
+    // interior and boundary chunks form one index range, so that with enough
+    // CTAs every CTA handles a single patch per colour
+    const long long chi = (g.n_int + Cfg::PPC_I - 1) / Cfg::PPC_I;
+    const long long chb = (g.n_bnd + Cfg::PPC_B - 1) / Cfg::PPC_B;
+    for (long long q = blockIdx.x; q < (chi + chb) * nrhs; q += gridDim.x) {
+      const long long r = q / (chi + chb), ch = q % (chi + chb);
+      if (ch < chi)
+        smooth_chunk<DIM, NN, false, T, Cfg::PPC_I, true>(opsi, pre_i, base, ch * Cfg::PPC_I, c, b + r * ndofs,
+                                                          x + r * ndofs, N, consistent, g);
+      else
+        smooth_chunk<DIM, NN, true, T, Cfg::PPC_B, true>(opsb, pre_b, base, (ch - chi) * Cfg::PPC_B, c,
+                                                         b + r * ndofs, x + r * ndofs, N, consistent, g);
+      __syncthreads();  // the next chunk reuses (and re-lays out) the slots
+    }
+    if (ci + 1 < nc && !grid_barrier(bar, status, gridDim.x)) return;
+  }
+}
+
+// Self test of the bounded wait: a barrier expecting `extra` more CTAs than
+// were launched can never open, so every CTA must give up and set *status.
+__global__ void barrier_selftest_kernel(unsigned int* bar, int* status, int extra) {
+  grid_barrier(bar, status, gridDim.x + (unsigned int)extra);
+}
+
+PatchGrid make_grid(int dim, int N, int colour) {
   PatchGrid g;
   long long tot = 1, inner = 1;
   for (int e = 0; e < 3; ++e) {
-    if (e < DIM) {
+    if (e < dim) {
       const int par = (colour >> e) & 1;
       g.cnt[e] = par ? N / 2 : N / 2 - 1;
       g.lo[e] = par ? 1 : 0;
-      g.hi[e] = par ? N / 2 - 1 : N / 2 - 1;
+      g.hi[e] = N / 2 - 1;
       if (g.hi[e] < g.lo[e]) g.hi[e] = g.lo[e];
     } else {
       g.cnt[e] = 1;
       g.lo[e] = 0;
       g.hi[e] = 1;
     }
-    tot *= g.cnt[e];
+    tot *= g.cnt[e] > 0 ? g.cnt[e] : 0;
     inner *= (g.hi[e] - g.lo[e]);
   }
-  if (tot <= 0) return cudaSuccess;  // no patch of this colour (N = 2)
-  g.n_int = inner;
-  g.n_bnd = tot - inner;
-  cudaError_t e = launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s);
-  if (e != cudaSuccess) return e;
-  return launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, s);
+  if (tot <= 0) {
+    g.n_int = g.n_bnd = 0;
+  } else {
+    g.n_int = inner;
+    g.n_bnd = tot - inner;
+  }
+  return g;
+}
+
+// Returns cudaErrorNotSupported when the fused path does not apply (the caller
+// then launches the colours one by one).
+template <typename T, int DIM, int NN>
+cudaError_t step_dispatch2(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s) {
+  using Cfg = StepCfg<DIM, NN, T>;
+  if (Cfg::SMEM > 227 * 1024 || h->num_sms <= 0) return cudaErrorNotSupported;
+  static int max_active = -1;
+  if (max_active < 0) {
+    cudaError_t e = cudaFuncSetAttribute(smooth_step_kernel<DIM, NN, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smooth_step_kernel<DIM, NN, T>, Cfg::THREADS, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    max_active = nb;
+  }
+  if (max_active <= 0) return cudaErrorNotSupported;
+  const int N = h->lv[level].N;
+  StepGrids sg;
+  long long most = 0;
+  for (int c = 0; c < (1 << DIM); ++c) {
+    sg.g[c] = make_grid(DIM, N, c);
+    long long ch = (sg.g[c].n_int + Cfg::PPC_I - 1) / Cfg::PPC_I;
+    long long cb = (sg.g[c].n_bnd + Cfg::PPC_B - 1) / Cfg::PPC_B;
+    most = std::max(most, (ch + cb) * (long long)h->prm.nrhs);
+  }
+  const long long resident = (long long)max_active * h->num_sms;
+  if (most > resident) return cudaErrorNotSupported;  // several waves: per-colour launches
+  SmoothOps<SC<DIM, NN, false, T>::PO, SC<DIM, NN, false, T>::P, T, 1> opsi;
+  SmoothOps<SC<DIM, NN, true, T>::PO, SC<DIM, NN, true, T>::P, T, 4> opsb;
+  make_ops<SC<DIM, NN, false, T>::PO, SC<DIM, NN, false, T>::P, false, T>(h->hcst<T>(level), 0, opsi.t[0]);
+  for (int t = 0; t < 4; ++t)
+    make_ops<SC<DIM, NN, true, T>::PO, SC<DIM, NN, true, T>::P, true, T>(h->hcst<T>(level), t, opsb.t[t]);
+  const unsigned grid = (unsigned)std::max<long long>(1, most);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(Cfg::THREADS);
+  cfg.dynamicSmemBytes = Cfg::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  unsigned int* bar = reinterpret_cast<unsigned int*>(h->ws + h->off_sync);
+  int* status = reinterpret_cast<int*>(h->ws + h->off_sync + 2 * sizeof(unsigned int));
+  return cudaLaunchKernelEx(&cfg, smooth_step_kernel<DIM, NN, T>, opsi, opsb, reverse, b, x, N,
+                            h->prm.smoother == SIPG_SMOOTHER_CONSISTENT ? 1 : 0, (long long)h->lv[level].ndofs,
+                            h->prm.nrhs, sg, bar, status);
 }
 
 }  // namespace
@@ -785,3 +974,65 @@ template cudaError_t launch_smooth_colour<double>(const sipg_handle*, int, int, 
                                                   cudaStream_t);
 template cudaError_t launch_smooth_colour<float>(const sipg_handle*, int, int, const float*, float*,
                                                  cudaStream_t);
+
+template <typename T>
+cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s,
+                               int* launches) {
+  cudaError_t e = cudaErrorNotSupported;
+  if (h->fuse_small_levels) {
+    if (h->prm.dim == 2) {
+      switch (h->n) {
+        case 2: e = step_dispatch2<T, 2, 2>(h, level, reverse, b, x, s); break;
+        case 3: e = step_dispatch2<T, 2, 3>(h, level, reverse, b, x, s); break;
+        case 4: e = step_dispatch2<T, 2, 4>(h, level, reverse, b, x, s); break;
+        case 5: e = step_dispatch2<T, 2, 5>(h, level, reverse, b, x, s); break;
+        case 6: e = step_dispatch2<T, 2, 6>(h, level, reverse, b, x, s); break;
+        case 7: e = step_dispatch2<T, 2, 7>(h, level, reverse, b, x, s); break;
+        case 8: e = step_dispatch2<T, 2, 8>(h, level, reverse, b, x, s); break;
+      }
+    } else {
+      switch (h->n) {
+        case 2: e = step_dispatch2<T, 3, 2>(h, level, reverse, b, x, s); break;
+        case 3: e = step_dispatch2<T, 3, 3>(h, level, reverse, b, x, s); break;
+        case 4: e = step_dispatch2<T, 3, 4>(h, level, reverse, b, x, s); break;
+        case 5: e = step_dispatch2<T, 3, 5>(h, level, reverse, b, x, s); break;
+        case 6: e = step_dispatch2<T, 3, 6>(h, level, reverse, b, x, s); break;
+        case 7: e = step_dispatch2<T, 3, 7>(h, level, reverse, b, x, s); break;
+        case 8: e = step_dispatch2<T, 3, 8>(h, level, reverse, b, x, s); break;
+      }
+    }
+    if (e == cudaSuccess) {
+      *launches = 1;
+      return cudaSuccess;
+    }
+    if (e != cudaErrorNotSupported) return e;
+  }
+  const int nc = 1 << h->prm.dim;
+  *launches = 0;
+  for (int i = 0; i < nc; ++i) {
+    const int c = reverse ? nc - 1 - i : i;
+    e = launch_smooth_colour<T>(h, level, c, b, x, s);
+    if (e != cudaSuccess) return e;
+    *launches += 2;
+  }
+  return cudaSuccess;
+}
+template cudaError_t launch_smooth_step<double>(const sipg_handle*, int, int, const double*, double*, cudaStream_t,
+                                                int*);
+template cudaError_t launch_smooth_step<float>(const sipg_handle*, int, int, const float*, float*, cudaStream_t,
+                                               int*);
+
+cudaError_t launch_barrier_selftest(const sipg_handle* h, int extra, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  unsigned int* bar = reinterpret_cast<unsigned int*>(h->ws + h->off_sync);
+  int* status = reinterpret_cast<int*>(h->ws + h->off_sync + 2 * sizeof(unsigned int));
+  return cudaLaunchKernelEx(&cfg, barrier_selftest_kernel, bar, status, extra);
+}

@@ -333,3 +333,25 @@ def test_single_level_is_direct():
     info = s.solve(dev(b), xd, rtol=1e-12)
     assert info.iterations == 1
     assert rel_inf(host(xd), np.linalg.solve(A.toarray(), b)) < 1e-11
+
+
+@pytest.mark.parametrize("case", [(3, 3, 3, 2), (3, 2, 4, 3), (2, 4, 4, 2), (3, 3, 2, 2)])
+@pytest.mark.parametrize("prec", [SIPG_FP64, SIPG_FP32], ids=["fp64", "fp32"])
+def test_fused_step_equals_colour_passes(case, prec):
+    # one smoothing step launched as a single cooperative kernel (small
+    # levels) gives bit-identical results to the colour-by-colour launches
+    import torch
+    dim, k, l2, nl = case
+    dt = torch.float64 if prec == SIPG_FP64 else torch.float32
+    s = make(dim, k, l2, nl, prec=prec)
+    n = s.ndofs()
+    b = dev(inputs.normal(960, n), dt)
+    x0 = inputs.normal(961, n)
+    for reverse in (False, True):
+        xa = dev(x0, dt)
+        s.smooth(nl - 1, b, xa, reverse=reverse)
+        xb = dev(x0, dt)
+        order = range(2 ** dim)
+        for c in (reversed(order) if reverse else order):
+            s.smooth_colour(nl - 1, c, b, xb)
+        assert torch.equal(xa, xb)
