@@ -236,6 +236,43 @@ def block_apply(dim, k, N, blocks, x, cells_sel=None):
     return y
 
 
+def principal_block(dim, k, N, blocks, cells_sel):
+    """Dense A[D, D] for D = all DoFs of the listed cells (flat cell numbers,
+    in the given order, n^d DoFs each), from the element blocks: a cell's
+    diagonal block is its cell block plus the self parts of its faces; two
+    listed cells sharing a face couple through that face's off-diagonal block.
+    For the vertex-patch cells this is the patch matrix of Sec. 3.1 before
+    restriction to V_j, on meshes too large to assemble."""
+    n = k + 1
+    nl = n ** dim
+    allc = cell_multi_index(dim, N)
+    cells_sel = [int(c) for c in cells_sel]
+    pos = {c: i for i, c in enumerate(cells_sel)}
+    out = np.zeros((len(cells_sel) * nl, len(cells_sel) * nl))
+    strides = N ** np.arange(dim)
+    for i, c in enumerate(cells_sel):
+        cm = allc[c]
+        D = blocks["cell"].copy()
+        for e in range(dim):
+            B = blocks[("int", e)]
+            if cm[e] > 0:
+                D += B[1][1]
+                j = pos.get(c - int(strides[e]))
+                if j is not None:
+                    out[i * nl:(i + 1) * nl, j * nl:(j + 1) * nl] += B[1][0]
+            else:
+                D += blocks[("bnd", e, 0)]
+            if cm[e] < N - 1:
+                D += B[0][0]
+                j = pos.get(c + int(strides[e]))
+                if j is not None:
+                    out[i * nl:(i + 1) * nl, j * nl:(j + 1) * nl] += B[0][1]
+            else:
+                D += blocks[("bnd", e, 1)]
+        out[i * nl:(i + 1) * nl, i * nl:(i + 1) * nl] += D
+    return out
+
+
 def mass_matrix_cell(dim, k, N):
     """Exact cell mass matrix (k+1 Gauss points per direction)."""
     return cell_matrices(dim, k, N)[1]

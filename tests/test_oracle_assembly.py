@@ -99,6 +99,21 @@ def test_block_apply_equals_sparse_matrix(dim, k, N):
     assert np.allclose(ys, (A @ x).reshape(-1, n)[sel], atol=1e-12 * np.abs(A @ x).max())
 
 
+@pytest.mark.parametrize("dim,k,N", [(2, 2, 5), (3, 2, 4)])
+def test_principal_block_equals_assembled_submatrix(dim, k, N):
+    from oracle.assembly import principal_block
+    from oracle.layout import dof_index
+    A = assemble(dim, k, N, kappa=1.3).toarray()
+    blocks = element_blocks(dim, k, N, kappa=1.3)
+    n = k + 1
+    rng = np.random.default_rng(2)
+    for cells in ([0, 1, N, N + 1], list(rng.choice(N ** dim, size=6, replace=False)), [N ** dim - 1]):
+        D = np.concatenate([np.arange(n ** dim) + c * n ** dim for c in cells])
+        # same entries up to the summation order of the face contributions
+        sub = A[np.ix_(D, D)]
+        assert np.max(np.abs(principal_block(dim, k, N, blocks, cells) - sub)) <= 1e-14 * np.abs(A).max()
+
+
 @pytest.mark.parametrize("dim,k,N", [(1, 3, 5), (2, 2, 4), (3, 2, 2)])
 def test_rhs_partition_of_unity(dim, k, N):
     # sum_I int f phi_I = int f for f = 1: the total mass is 1
