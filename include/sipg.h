@@ -190,6 +190,30 @@ sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host
  * written to device memory. */
 sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* out, void* stream);
 
+/* ---- ragged batch: independent problems (any dim, degree, size) solved
+ * together.  Each member is a full handle (its own levels, workspace slice,
+ * CUDA graph); sipg_batch_solve advances all members' flexible CG iterations
+ * in lockstep, each on its own internal stream joined to `stream` by events,
+ * so the members' kernels overlap on the GPU and the host waits once per
+ * round.  Members converge independently. */
+typedef struct sipg_batch sipg_batch;
+sipg_status sipg_batch_create(const sipg_params* params, int count, sipg_batch** out);
+void sipg_batch_destroy(sipg_batch* b);
+const char* sipg_batch_last_error(const sipg_batch* b);
+int sipg_batch_count(const sipg_batch* b);
+/* Member i (owned by the batch): use it for sipg_ndofs, sipg_rhs, ... */
+sipg_handle* sipg_batch_member(sipg_batch* b, int i);
+/* Sum of the members' workspaces (each 256-byte aligned inside). */
+size_t sipg_batch_workspace_bytes(const sipg_batch* b);
+/* Bind one caller-owned buffer for all members (runs every member's setup). */
+sipg_status sipg_batch_bind_workspace(sipg_batch* b, void* dev_ptr, size_t bytes, void* stream);
+/* b[i], x[i]: device vectors of member i (host arrays of count pointers);
+ * x[i] holds the initial guess on entry.  infos: NULL or count entries.
+ * Returns the first member failure (sipg_batch_last_error names it).
+ * Synchronises the internal streams. */
+sipg_status sipg_batch_solve(sipg_batch* b, const double* const* bvecs, double* const* xvecs, double rtol,
+                             int maxit, sipg_info* infos, void* stream);
+
 /* Same result as sipg_dot, for callers that cannot allocate device memory
  * (an application whose allocator already holds all of it, or a latency path
  * where cudaMalloc would synchronise the device): needs a created handle (for

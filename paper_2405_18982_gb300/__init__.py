@@ -15,7 +15,7 @@ from . import _binding as B
 from ._binding import (SIPG_FP32, SIPG_FP64, SIPG_SMOOTHER_CONSISTENT, SIPG_SMOOTHER_PAPER,
                        SipgError, load)
 
-__all__ = ["Params", "SIPG", "SipgError", "SIPG_FP64", "SIPG_FP32",
+__all__ = ["Params", "SIPG", "SIPGBatch", "SipgError", "SIPG_FP64", "SIPG_FP32",
            "SIPG_SMOOTHER_CONSISTENT", "SIPG_SMOOTHER_PAPER", "load", "build"]
 
 
@@ -81,6 +81,7 @@ class SIPG:
     def __init__(self, params, device=None, stream=None):
         import torch
         self.lib = load()
+        self._owned = True
         self.params = params
         self._cp = params.to_c()
         h = ctypes.c_void_p()
@@ -110,9 +111,9 @@ class SIPG:
         return st
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", False):
             self.lib.sipg_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -214,3 +215,75 @@ class SIPG:
         self._check(self.lib.sipg_get_constants(self.h, level, which, ptype, buf, cap, ctypes.byref(cnt),
                                                 self._stream(stream)))
         return np.array(buf[:min(cnt.value, cap)])
+
+
+class SIPGBatch:
+    """A ragged batch of independent problems (``sipg_batch_*``): one workspace
+    for all members, solved together with ``solve`` (each member on its own
+    stream, the flexible CG iterations advancing in lockstep)."""
+
+    def __init__(self, params_list, device=None, stream=None):
+        import torch
+        self.lib = load()
+        self.params = list(params_list)
+        arr = (B.sipg_params * len(self.params))(*[p.to_c() for p in self.params])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        st = self.lib.sipg_batch_create(arr, len(self.params), ctypes.byref(h))
+        if st != 0:
+            raise SipgError(st, "sipg_batch_create rejected the parameters")
+        self.h = h
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        nbytes = self.lib.sipg_batch_workspace_bytes(self.h)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) & ~255
+        self._check(self.lib.sipg_batch_bind_workspace(self.h, ctypes.c_void_p(aligned), nbytes,
+                                                       self._stream(stream)))
+        self.members = []
+        for i, p in enumerate(self.params):
+            m = SIPG.__new__(SIPG)
+            m.lib, m.params, m._owned, m.device = self.lib, p, False, self.device
+            m.h = ctypes.c_void_p(self.lib.sipg_batch_member(self.h, i))
+            self.members.append(m)
+
+    def __len__(self):
+        return len(self.members)
+
+    def _stream(self, stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _check(self, st):
+        if st != 0:
+            msg = self.lib.sipg_batch_last_error(self.h)
+            raise SipgError(st, msg.decode() if msg else "")
+        return st
+
+    def solve(self, bs, xs, rtol=1e-10, maxit=200, stream=None, history=64, allow_noconv=False):
+        """bs, xs: lists of member vectors (contiguous CUDA float64)."""
+        n = len(self.members)
+        if len(bs) != n or len(xs) != n:
+            raise ValueError("one b and one x per member")
+        bp = (ctypes.c_void_p * n)(*[_ptr(b).value for b in bs])
+        xp = (ctypes.c_void_p * n)(*[_ptr(x).value for x in xs])
+        hists = [(ctypes.c_double * history)() for _ in range(n)]
+        infos = (B.sipg_info * n)(*[B.sipg_info(0, 0, 0.0, 0.0, hists[i], history, 0) for i in range(n)])
+        st = self.lib.sipg_batch_solve(self.h, bp, xp, rtol, maxit, infos, self._stream(stream))
+        if st != 0 and not (allow_noconv and st == B.SIPG_ENOCONV):
+            self._check(st)
+        return [SolveInfo(infos[i].iterations, infos[i].status, infos[i].rel_residual, infos[i].nu,
+                          [hists[i][j] for j in range(infos[i].history_len)]) for i in range(n)]
+
+    def close(self):
+        for m in getattr(self, "members", []):
+            m.h = None
+        if getattr(self, "h", None):
+            self.lib.sipg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -75,6 +75,15 @@ SIGNATURES = {
     "sipg_dot_noalloc": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_selftest_barrier": (_st, [_vp, _i, _vp]),
     "sipg_get_constants": (_st, [_vp, _i, _i, _i, _vp, _i, ctypes.POINTER(_i), _vp]),
+    "sipg_batch_create": (_st, [ctypes.POINTER(sipg_params), _i, ctypes.POINTER(_vp)]),
+    "sipg_batch_destroy": (None, [_vp]),
+    "sipg_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "sipg_batch_count": (_i, [_vp]),
+    "sipg_batch_member": (_vp, [_vp, _i]),
+    "sipg_batch_workspace_bytes": (ctypes.c_size_t, [_vp]),
+    "sipg_batch_bind_workspace": (_st, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "sipg_batch_solve": (_st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
+                               ctypes.POINTER(sipg_info), _vp]),
 }
 
 _lib = None

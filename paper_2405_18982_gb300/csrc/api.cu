@@ -127,15 +127,6 @@ sipg_status iteration_body(sipg_handle* h, double* x, cudaStream_t s) {
   return step_update(h, x, s);
 }
 
-sipg_status read_scalars(sipg_handle* h, std::vector<KrylovScalars>& out, cudaStream_t s) {
-  out.resize(h->prm.nrhs);
-  SIPG_CHECK(cudaMemcpyAsync(out.data(), h->scalars(), sizeof(KrylovScalars) * h->prm.nrhs,
-                             cudaMemcpyDeviceToHost, s),
-             "scalars D2H");
-  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
-  return SIPG_OK;
-}
-
 // Capture one iteration body as a CUDA graph (on the internal stream).
 sipg_status ensure_graph(sipg_handle* h, double* x) {
   if (h->iter_exec && h->g_x == x) return SIPG_OK;
@@ -178,70 +169,115 @@ sipg_status run_body(sipg_handle* h, double* x, cudaStream_t s) {
   return SIPG_OK;
 }
 
-sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
-                      sipg_info* info, cudaStream_t s) {
-  const int nr = h->prm.nrhs;
-  h->rtol2 = rtol * rtol;
-  std::vector<KrylovScalars> sc;
-  std::vector<double> hist0;
-  int it = 0;
+// Flexible CG as a state machine, so that several independent problems (a
+// batch) can advance in lockstep, each on its own stream: every step launches
+// GPU work and an asynchronous copy of the Krylov scalars, the driver waits
+// once for all pending problems, then each problem takes its host decision.
+// For one problem the launch sequence is: true residual; first direction;
+// iterations until convergence, breakdown or maxit; true residual again
+// (restarting, at most 4 times, if the recursively updated residual drifted
+// below the true one).
+struct FcgRun {
+  sipg_handle* h = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  cudaStream_t s = nullptr;
+  int maxit = 0;
+  sipg_info* info = nullptr;
+  enum Phase { INITIAL, FIRST, ITERATE, VERIFY, DONE } phase = INITIAL;
+  bool pending = false;     // GPU work in flight whose scalars must be read
+  int it = 0, restarts = 0;
   sipg_status result = SIPG_OK;
-  double r0 = 0.0;
-  bool first_start = true;
-  auto any_breakdown = [&]() {
-    for (int c = 0; c < nr; ++c)
-      if (sc[c].breakdown) return true;
-    return false;
-  };
-  auto any_active = [&]() {
-    for (int c = 0; c < nr; ++c)
-      if (sc[c].active) return true;
-    return false;
-  };
-  // true residual r = b - A x and the norms ||b||, ||r|| (sets the active flags)
-  auto true_residual = [&]() -> sipg_status {
-    SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_RESIDUAL, b, x, h->kr(), s), "residual");
-    h->launches += 1;
-    SIPG_CHECK(krylov_init_norms(h, b, h->kr(), s), "norms");
-    return read_scalars(h, sc, s);
-  };
-  sipg_status st = true_residual();
-  if (st) return st;
-  r0 = sqrt(sc[0].rr);
-  hist0.push_back(r0);
-  (void)first_start;
-  // restarts only happen if the recursively updated residual met rtol while
-  // the true one did not
-  for (int restart = 0; restart < 4 && result == SIPG_OK; ++restart) {
-    if (any_breakdown()) {
-      result = SIPG_EBREAKDOWN;
-      break;
-    }
-    if (!any_active() || it >= maxit) break;
-    st = precondition(h, 1, s);  // z_0 = B r_0, p_0 = z_0
-    if (st) return st;
-    st = step_update(h, x, s);
-    if (st) return st;
-    ++it;
-    st = read_scalars(h, sc, s);
-    if (st) return st;
-    hist0.push_back(sqrt(sc[0].rr));
-    while (!any_breakdown() && any_active() && it < maxit) {
-      st = run_body(h, x, s);
+  std::vector<double> hist;
+};
+
+bool run_any(const sipg_handle* h, bool (*pred)(const KrylovScalars&)) {
+  for (int c = 0; c < h->prm.nrhs; ++c)
+    if (pred(h->pinned[c])) return true;
+  return false;
+}
+bool is_active(const KrylovScalars& k) { return k.active != 0; }
+bool is_broken(const KrylovScalars& k) { return k.breakdown != 0; }
+
+sipg_status queue_scalars(FcgRun& r) {
+  sipg_handle* h = r.h;
+  SIPG_CHECK(cudaMemcpyAsync(h->pinned, h->scalars(), sizeof(KrylovScalars) * h->prm.nrhs, cudaMemcpyDeviceToHost,
+                             r.s),
+             "scalars D2H");
+  r.pending = true;
+  return SIPG_OK;
+}
+
+sipg_status launch_true_residual(FcgRun& r) {
+  sipg_handle* h = r.h;
+  SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_RESIDUAL, r.b, r.x, h->kr(), r.s), "residual");
+  h->launches += 1;
+  SIPG_CHECK(krylov_init_norms(h, r.b, h->kr(), r.s), "norms");
+  return queue_scalars(r);
+}
+
+// Host decisions after the scalars of the last step arrived; launches the
+// next step (or finishes the run).
+sipg_status advance(FcgRun& r) {
+  sipg_handle* h = r.h;
+  sipg_status st = SIPG_OK;
+  switch (r.phase) {
+    case FcgRun::INITIAL:
+      if (!r.pending) return launch_true_residual(r);
+      r.pending = false;
+      r.hist.push_back(sqrt(h->pinned[0].rr));
+      r.phase = FcgRun::VERIFY;
+      r.restarts = -1;  // the initial residual is not a restart
+      return advance(r);
+    case FcgRun::VERIFY:
+      // true residual known: finish, or (re)start the iteration
+      r.pending = false;
+      ++r.restarts;
+      if (run_any(h, is_broken)) {
+        r.result = SIPG_EBREAKDOWN;
+        r.phase = FcgRun::DONE;
+        return SIPG_OK;
+      }
+      if (!run_any(h, is_active) || r.it >= r.maxit || r.restarts >= 4) {
+        r.phase = FcgRun::DONE;
+        return SIPG_OK;
+      }
+      st = precondition(h, 1, r.s);  // z_0 = B r_0, p_0 = z_0
       if (st) return st;
-      ++it;
-      st = read_scalars(h, sc, s);
+      st = step_update(h, r.x, r.s);
       if (st) return st;
-      hist0.push_back(sqrt(sc[0].rr));
-    }
-    if (any_breakdown()) {
-      result = SIPG_EBREAKDOWN;
-      break;
-    }
-    st = true_residual();
-    if (st) return st;
+      r.phase = FcgRun::FIRST;
+      return queue_scalars(r);
+    case FcgRun::FIRST:
+    case FcgRun::ITERATE:
+      r.pending = false;
+      ++r.it;
+      r.hist.push_back(sqrt(h->pinned[0].rr));
+      if (run_any(h, is_broken)) {
+        r.result = SIPG_EBREAKDOWN;
+        r.phase = FcgRun::DONE;
+        return SIPG_OK;
+      }
+      if (run_any(h, is_active) && r.it < r.maxit) {
+        st = run_body(h, r.x, r.s);
+        if (st) return st;
+        r.phase = FcgRun::ITERATE;
+        return queue_scalars(r);
+      }
+      r.phase = FcgRun::VERIFY;
+      return launch_true_residual(r);
+    case FcgRun::DONE:
+      return SIPG_OK;
   }
-  if (result == SIPG_OK && any_breakdown()) result = SIPG_EBREAKDOWN;
+  return SIPG_OK;
+}
+
+sipg_status finish(FcgRun& r) {
+  sipg_handle* h = r.h;
+  const int nr = h->prm.nrhs;
+  const KrylovScalars* sc = h->pinned;
+  sipg_status result = r.result;
+  if (result == SIPG_OK && run_any(h, is_broken)) result = SIPG_EBREAKDOWN;
   double worst = 0.0;
   bool all_conv = true;
   for (int c = 0; c < nr; ++c) {
@@ -250,20 +286,21 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
     if (sc[c].active) all_conv = false;
   }
   if (result == SIPG_OK && !all_conv) result = SIPG_ENOCONV;
+  sipg_info* info = r.info;
   if (info) {
-    info->iterations = it;
+    info->iterations = r.it;
     info->status = result;
     info->rel_residual = worst;
     double nu = 0.0;
-    if (it > 0 && hist0.size() > 1 && hist0.front() > 0.0) {
-      double rbar = pow(hist0.back() / hist0.front(), 1.0 / (double)(hist0.size() - 1));
+    if (r.it > 0 && r.hist.size() > 1 && r.hist.front() > 0.0) {
+      double rbar = pow(r.hist.back() / r.hist.front(), 1.0 / (double)(r.hist.size() - 1));
       nu = (rbar > 0.0 && rbar < 1.0) ? -8.0 / log10(rbar) : INFINITY;
     }
     info->nu = nu;
     int cnt = 0;
     if (info->history && info->history_capacity > 0) {
-      cnt = std::min((int)hist0.size(), info->history_capacity);
-      for (int i = 0; i < cnt; ++i) info->history[i] = hist0[i];
+      cnt = std::min((int)r.hist.size(), info->history_capacity);
+      for (int i = 0; i < cnt; ++i) info->history[i] = r.hist[i];
     }
     info->history_len = cnt;
   }
@@ -271,11 +308,11 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
     // a bounded grid-barrier wait that ran out (fused smoothing steps)
     int status = 0;
     SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_sync + 2 * sizeof(unsigned int), sizeof(int),
-                               cudaMemcpyDeviceToHost, s),
+                               cudaMemcpyDeviceToHost, r.s),
                "status D2H");
-    SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+    SIPG_CHECK(cudaStreamSynchronize(r.s), "sync");
     if (status != 0) {
-      SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+      SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, r.s), "memset");
       h->err = "a bounded grid-barrier wait in the smoother timed out";
       if (info) info->status = SIPG_ETIMEOUT;
       return SIPG_ETIMEOUT;
@@ -284,6 +321,45 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
   if (result == SIPG_ENOCONV) h->err = "solver reached maxit before rtol";
   if (result == SIPG_EBREAKDOWN) h->err = "Krylov breakdown (non-finite or non-positive scalar)";
   return result;
+}
+
+// Drive several runs to completion; the first CUDA-level failure aborts.
+sipg_status drive(std::vector<FcgRun>& runs) {
+  for (auto& r : runs) {
+    sipg_status st = advance(r);
+    if (st) return st;
+  }
+  for (;;) {
+    bool any = false;
+    for (auto& r : runs) {
+      if (!r.pending) continue;
+      any = true;
+      cudaError_t e = cudaStreamSynchronize(r.s);
+      if (e != cudaSuccess) return cuda_fail(r.h, e, "sync");
+    }
+    if (!any) break;
+    for (auto& r : runs) {
+      if (!r.pending) continue;
+      sipg_status st = advance(r);
+      if (st) return st;
+    }
+  }
+  return SIPG_OK;
+}
+
+sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
+                      sipg_info* info, cudaStream_t s) {
+  h->rtol2 = rtol * rtol;
+  std::vector<FcgRun> runs(1);
+  runs[0].h = h;
+  runs[0].b = b;
+  runs[0].x = x;
+  runs[0].s = s;
+  runs[0].maxit = maxit;
+  runs[0].info = info;
+  sipg_status st = drive(runs);
+  if (st) return st;
+  return finish(runs[0]);
 }
 
 }  // namespace
@@ -383,6 +459,10 @@ void sipg_destroy(sipg_handle* h) {
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->ev_a) cudaEventDestroy(h->ev_a);
   if (h->ev_b) cudaEventDestroy(h->ev_b);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 
@@ -413,6 +493,15 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
     int dev = 0;
     SIPG_CHECK(cudaGetDevice(&dev), "device");
     SIPG_CHECK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  }
+  if (!h->pinned)  // page-locked host memory for the per-iteration scalar read-back
+    SIPG_CHECK(cudaHostAlloc(reinterpret_cast<void**>(&h->pinned), sizeof(KrylovScalars) * h->prm.nrhs,
+                             cudaHostAllocDefault),
+               "pinned host buffer");
+  if (!h->side) {
+    SIPG_CHECK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
+    SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "event");
+    SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");
   }
   SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
   SIPG_CHECK(launch_setup(h, s), "setup");
@@ -689,6 +778,143 @@ sipg_status sipg_get_constants(sipg_handle* h, int level, int which, int type, d
   for (int i = 0; i < cnt; ++i) host_out[i] = v[i];
   *count = (int)v.size();
   return SIPG_OK;
+}
+
+// ------------------------------------------------------------------ ragged batch
+struct sipg_batch {
+  std::vector<sipg_handle*> hs;
+  std::vector<size_t> off;
+  size_t ws_bytes = 0;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t start = nullptr;
+  std::string err;
+};
+
+sipg_status sipg_batch_create(const sipg_params* params, int count, sipg_batch** out) {
+  if (!out) return SIPG_EINVAL;
+  *out = nullptr;
+  if (!params || count < 1 || count > 4096) return SIPG_EINVAL;
+  sipg_batch* bt = new sipg_batch();
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    sipg_handle* h = nullptr;
+    sipg_status st = sipg_create(&params[i], &h);
+    if (st != SIPG_OK) {
+      for (auto* g : bt->hs) sipg_destroy(g);
+      delete bt;
+      return st;
+    }
+    // the members' kernels run concurrently on separate streams, so no member
+    // relies on a cooperative launch having the whole GPU to itself
+    h->fuse_small_levels = false;
+    bt->hs.push_back(h);
+    bt->off.push_back(off);
+    off += align256(sipg_workspace_bytes(h));
+  }
+  bt->ws_bytes = off;
+  *out = bt;
+  return SIPG_OK;
+}
+
+void sipg_batch_destroy(sipg_batch* bt) {
+  if (!bt) return;
+  for (auto* h : bt->hs) sipg_destroy(h);
+  for (auto s : bt->streams) cudaStreamDestroy(s);
+  for (auto e : bt->done) cudaEventDestroy(e);
+  if (bt->start) cudaEventDestroy(bt->start);
+  delete bt;
+}
+
+const char* sipg_batch_last_error(const sipg_batch* bt) { return bt ? bt->err.c_str() : "null batch"; }
+
+size_t sipg_batch_workspace_bytes(const sipg_batch* bt) { return bt ? bt->ws_bytes : 0; }
+
+int sipg_batch_count(const sipg_batch* bt) { return bt ? (int)bt->hs.size() : 0; }
+
+sipg_handle* sipg_batch_member(sipg_batch* bt, int i) {
+  if (!bt || i < 0 || i >= (int)bt->hs.size()) return nullptr;
+  return bt->hs[i];
+}
+
+sipg_status sipg_batch_bind_workspace(sipg_batch* bt, void* dev_ptr, size_t bytes, void* stream) {
+  if (!bt) return SIPG_EINVAL;
+  if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 255) || bytes < bt->ws_bytes) {
+    bt->err = "workspace pointer null, misaligned or too small";
+    return dev_ptr ? SIPG_ENOMEM_WORKSPACE : SIPG_EINVAL;
+  }
+  for (size_t i = 0; i < bt->hs.size(); ++i) {
+    sipg_handle* h = bt->hs[i];
+    sipg_status st = sipg_bind_workspace(h, static_cast<char*>(dev_ptr) + bt->off[i], sipg_workspace_bytes(h),
+                                         stream);
+    if (st != SIPG_OK) {
+      bt->err = "member " + std::to_string(i) + ": " + h->err;
+      return st;
+    }
+  }
+  if (bt->streams.empty()) {
+    bt->streams.resize(bt->hs.size());
+    bt->done.resize(bt->hs.size());
+    for (size_t i = 0; i < bt->hs.size(); ++i) {
+      if (cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&bt->done[i], cudaEventDisableTiming) != cudaSuccess) {
+        bt->err = "stream or event creation failed";
+        return SIPG_ECUDA;
+      }
+    }
+    if (cudaEventCreateWithFlags(&bt->start, cudaEventDisableTiming) != cudaSuccess) {
+      bt->err = "event creation failed";
+      return SIPG_ECUDA;
+    }
+  }
+  return SIPG_OK;
+}
+
+sipg_status sipg_batch_solve(sipg_batch* bt, const double* const* b, double* const* x, double rtol, int maxit,
+                             sipg_info* infos, void* stream) {
+  if (!bt || !b || !x || !(rtol > 0.0) || maxit < 0) return SIPG_EINVAL;
+  const size_t n = bt->hs.size();
+  for (size_t i = 0; i < n; ++i) {
+    if (!bt->hs[i]->bound || bt->streams.empty()) {
+      bt->err = "workspace not bound";
+      return SIPG_ESTATE;
+    }
+    if (!b[i] || !x[i] || b[i] == x[i]) {
+      bt->err = "member " + std::to_string(i) + ": null or aliased vectors";
+      return SIPG_EINVAL;
+    }
+  }
+  cudaStream_t cs = S(stream);
+  if (cudaEventRecord(bt->start, cs) != cudaSuccess) return SIPG_ECUDA;
+  std::vector<FcgRun> runs(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (cudaStreamWaitEvent(bt->streams[i], bt->start, 0) != cudaSuccess) return SIPG_ECUDA;
+    bt->hs[i]->rtol2 = rtol * rtol;
+    runs[i].h = bt->hs[i];
+    runs[i].b = b[i];
+    runs[i].x = x[i];
+    runs[i].s = bt->streams[i];
+    runs[i].maxit = maxit;
+    runs[i].info = infos ? &infos[i] : nullptr;
+  }
+  sipg_status st = drive(runs);
+  sipg_status worst = st;
+  for (size_t i = 0; i < n && st == SIPG_OK; ++i) {
+    sipg_status si = finish(runs[i]);
+    if (si != SIPG_OK && worst == SIPG_OK) {
+      worst = si;
+      bt->err = "member " + std::to_string(i) + ": " + bt->hs[i]->err;
+    }
+  }
+  if (st != SIPG_OK) {
+    for (size_t i = 0; i < n; ++i)
+      if (!bt->hs[i]->err.empty()) bt->err = "member " + std::to_string(i) + ": " + bt->hs[i]->err;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    cudaEventRecord(bt->done[i], bt->streams[i]);
+    cudaStreamWaitEvent(cs, bt->done[i], 0);
+  }
+  return worst;
 }
 
 }  // extern "C"

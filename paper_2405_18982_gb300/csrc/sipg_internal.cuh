@@ -96,7 +96,12 @@ struct sipg_handle {
   char* ws = nullptr;
   bool bound = false;
   int num_sms = 0;                           // of the device the workspace lives on
+  KrylovScalars* pinned = nullptr;           // page-locked host copy of the scalars (nrhs)
   bool fuse_small_levels = true;             // one cooperative launch per smoothing step when it fits one wave
+  // second stream for the boundary-patch kernel of a colour pass, forked
+  // from and joined to the calling stream with these events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // host copies of the device-computed level constants (read back once at
   // bind time; kernels receive the small 1D operators as launch parameters)
   std::vector<LevelConst<double>> hc64;

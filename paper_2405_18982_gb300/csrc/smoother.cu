@@ -758,7 +758,19 @@ template <typename T, int DIM, int NN>
 cudaError_t smooth_dispatch2(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s) {
   const PatchGrid g = make_grid(DIM, h->lv[level].N, colour);
   if (g.n_int + g.n_bnd <= 0) return cudaSuccess;  // no patch of this colour (N = 2)
-  cudaError_t e = launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s);
+  cudaError_t e;
+  if (g.n_int > 0 && g.n_bnd > 0 && h->side) {
+    // the boundary-patch kernel runs beside the interior one (patches of one
+    // colour write disjoint nodes and read none that another one writes), so
+    // its CTAs fill the SMs the interior grid leaves idle in its last wave
+    if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, h->side)) != cudaSuccess) return e;
+    if ((e = launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, h->ev_join, 0);
+  }
+  e = launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s);
   if (e != cudaSuccess) return e;
   return launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, s);
 }

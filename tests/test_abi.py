@@ -63,3 +63,32 @@ def test_host_only_calls_without_gpu(lib):
     assert b"workspace" in lib.sipg_last_error(h)
     lib.sipg_destroy(h)
     assert lib.sipg_version().startswith(b"sipg")
+
+
+def test_batch_host_only_calls_without_gpu(lib):
+    from paper_2405_18982_gb300._binding import SIGNATURES, sipg_params
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    b = ctypes.c_void_p()
+    arr = (sipg_params * 3)(sipg_params(2, 2, 5, 5, 1.0, 1.0, 1, 0, 1, 1),
+                            sipg_params(2, 6, 9, 9, 1.0, 1.0, 1, 0, 1, 1),
+                            sipg_params(2, 4, 7, 7, 1.0, 1.0, 1, 0, 1, 1))
+    assert lib.sipg_batch_create(arr, 0, ctypes.byref(b)) == -1 and not b.value
+    bad = (sipg_params * 2)(arr[0], sipg_params(2, 9, 5, 5, 1.0, 1.0, 1, 0, 1, 1))  # degree 9
+    assert lib.sipg_batch_create(bad, 2, ctypes.byref(b)) == -1 and not b.value
+    assert lib.sipg_batch_create(arr, 3, ctypes.byref(b)) == 0 and b.value
+    assert lib.sipg_batch_count(b) == 3
+    total = 0
+    for i, (L, k) in enumerate([(5, 2), (9, 6), (7, 4)]):
+        m = lib.sipg_batch_member(b, i)
+        assert m and lib.sipg_ndofs(m, L - 1) == (1 << L) ** 2 * (k + 1) ** 2
+        total += (lib.sipg_workspace_bytes(m) + 255) // 256 * 256
+    assert not lib.sipg_batch_member(b, 3)
+    assert lib.sipg_batch_workspace_bytes(b) == total
+    # solving before binding is rejected
+    ptrs = (ctypes.c_void_p * 3)(16, 16, 16)
+    xs = (ctypes.c_void_p * 3)(32, 32, 32)
+    assert lib.sipg_batch_solve(b, ptrs, xs, 1e-10, 10, None, None) == -8
+    assert b"bound" in lib.sipg_batch_last_error(b)
+    lib.sipg_batch_destroy(b)
