@@ -754,6 +754,16 @@ cudaError_t launch_part(const sipg_handle* h, int level, int colour, const T* b,
 
 PatchGrid make_grid(int dim, int N, int colour);
 
+#include "smooth_int3.cuh"
+
+template <int DIM, int NN, typename T>
+cudaError_t launch_interior(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
+                            cudaStream_t s) {
+  if constexpr (DIM == 3 && sizeof(T) == 4)
+    if (use_int3<DIM, T>(g, b, x)) return launch_int3<NN, T>(h, level, colour, b, x, g, s);
+  return launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s);
+}
+
 template <typename T, int DIM, int NN>
 cudaError_t smooth_dispatch2(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s) {
   const PatchGrid g = make_grid(DIM, h->lv[level].N, colour);
@@ -766,11 +776,11 @@ cudaError_t smooth_dispatch2(const sipg_handle* h, int level, int colour, const 
     if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if ((e = launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, h->side)) != cudaSuccess) return e;
-    if ((e = launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s)) != cudaSuccess) return e;
+    if ((e = launch_interior<DIM, NN, T>(h, level, colour, b, x, g, s)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     return cudaStreamWaitEvent(s, h->ev_join, 0);
   }
-  e = launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s);
+  e = launch_interior<DIM, NN, T>(h, level, colour, b, x, g, s);
   if (e != cudaSuccess) return e;
   return launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, s);
 }

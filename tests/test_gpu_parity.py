@@ -339,7 +339,9 @@ def test_single_level_is_direct():
 @pytest.mark.parametrize("prec", [SIPG_FP64, SIPG_FP32], ids=["fp64", "fp32"])
 def test_fused_step_equals_colour_passes(case, prec):
     # one smoothing step launched as a single cooperative kernel (small
-    # levels) gives bit-identical results to the colour-by-colour launches
+    # levels) gives the result of the colour-by-colour launches: bit-identical
+    # where both run the same patch kernel; 3D FP32 colour passes run the
+    # register-direct interior kernel (other summation order): FP32 rounding
     import torch
     dim, k, l2, nl = case
     dt = torch.float64 if prec == SIPG_FP64 else torch.float32
@@ -354,4 +356,7 @@ def test_fused_step_equals_colour_passes(case, prec):
         order = range(2 ** dim)
         for c in (reversed(order) if reverse else order):
             s.smooth_colour(nl - 1, c, b, xb)
-        assert torch.equal(xa, xb)
+        if dim == 3 and prec == SIPG_FP32:
+            assert rel_inf(host(xa), host(xb)) < 1e-5
+        else:
+            assert torch.equal(xa, xb)
