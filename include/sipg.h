@@ -37,6 +37,10 @@
  *
  * Errors: every call returns a sipg_status; failures never abort or trap.
  * sipg_last_error(h) returns a message for the last failure on h.
+ *
+ * Tuning (read by sipg_create): SIPG_FUSED_SMOOTHING=0 in the environment
+ * turns off the single cooperative launch per smoothing step on small levels
+ * (the colours are then launched one by one; the results are the same).
  */
 #ifndef SIPG_H
 #define SIPG_H

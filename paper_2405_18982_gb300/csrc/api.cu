@@ -4,6 +4,7 @@
 // caller's stream (or, for CUDA-graph replay, on an internal stream joined to
 // it by events).
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -394,6 +395,8 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
 
   sipg_handle* h = new sipg_handle();
   h->prm = *p;
+  // tuning knob: SIPG_FUSED_SMOOTHING=0 launches small levels colour by colour
+  if (const char* env = getenv("SIPG_FUSED_SMOOTHING")) h->fuse_small_levels = atoi(env) != 0;
   h->n = n;
   h->L = L;
   for (int l = 0; l <= L; ++l) {

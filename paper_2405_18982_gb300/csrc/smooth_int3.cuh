@@ -1,10 +1,10 @@
-// Interior vertex patches in 3D, register-direct variant of the colour pass
-// (Algorithm 1 with the fast-diagonalisation local solve of Eq. inverse3d).
-// Included by smoother.cu after its line-contraction helpers.
+// 3D vertex patches, register-direct variant of the colour pass (Algorithm 1
+// with the fast-diagonalisation local solve of Eq. inverse3d).  Included by
+// smoother.cu after its line-contraction helpers.
 //
 // Same arithmetic as the generic colour pass: the patch residual on V_j by
 // three sum-factorised sweeps (x, y, z) of the rows V_j of the 1D patch mass
-// and SIPG matrices, then u = (S x S x S) Lambda^{-1} (S x S x S)^T r and
+// and SIPG matrices, then u = (S_z x S_y x S_x) Lambda^{-1} (...)^T r and
 // x[V_j] += u.  What differs is the data movement, designed for the FP32 path
 // on GB300 where the generic kernel was bound by shared-memory wavefronts and
 // instruction issue rather than by HBM or the FMA pipe:
@@ -21,6 +21,12 @@
 //     straddle two patches stay conflict-free), and the x sweep stores pairs;
 //   * TPP = p^2 threads per patch (one line each in the z sweep and in every
 //     transform), several patches per CTA, six CTA barriers per colour pass.
+// Interior patches (BND = false) run with p = 2k rows per direction and the
+// operators as kernel parameters (constant-bank operands).  Patches touching
+// the domain boundary (BND = true) run with p = 2n rows: per direction one of
+// four operator sets (interior, low end, high end, both) read from shared
+// memory, rows outside V_j with zero operators, S padded by the identity, the
+// residual zeroed outside V_j and halos outside the domain read as zero.
 
 constexpr int i3_pad32(int m, int r) {
   int s = m;
@@ -29,12 +35,13 @@ constexpr int i3_pad32(int m, int r) {
 }
 constexpr int i3_max(int a, int b) { return a > b ? a : b; }
 
-template <int NN, typename T>
+template <int NN, typename T, bool BND>
 struct I3 {
-  static constexpr int P = 2 * NN;       // patch nodes per direction
-  static constexpr int PO = 2 * NN - 2;  // V_j rows per direction (interior)
+  static constexpr int P = 2 * NN;                      // patch nodes per direction
+  static constexpr int PO = BND ? 2 * NN : 2 * NN - 2;  // rows per direction
+  static constexpr int OFF = BND ? 0 : 1;               // patch node of row 0
   static constexpr int TPP = PO * PO;
-  static constexpr int W = (int)(sizeof(T) / 4);  // 32-bit words per element
+  static constexpr int NT = BND ? 4 : 1;                // operator sets
   // strides in elements; the bank rules are stated for 4-byte words and hold
   // for 8-byte elements accessed by half-warps
   static constexpr int SA1 = i3_pad32(P * PO, 16);   // A/B/halo rows (per a1 or halo slot)
@@ -45,7 +52,8 @@ struct I3 {
   static constexpr int RA = i3_max((2 * P + 4) * SA1, i3_max(PO * ST, PO * SQ));
   static constexpr int RB = i3_max(2 * P * SC + 2 * CZS, i3_max(PO * SQ, PO * ST));
   static constexpr int PS = i3_pad32(RA + RB, TPP);  // patch stride (elements)
-  static constexpr int DINV = PO * PO * PO;
+  // CTA prefix (interior): the table 1 / (lambda_k0 + lambda_k1 + lambda_k2)
+  static constexpr int DINV = BND ? 0 : PO * PO * PO;
   static constexpr int PREFIX = (DINV * (int)sizeof(T) + 15) / 16 * 16;
   // patches per CTA: fill about 54 KB of shared memory (four CTAs per SM) with
   // at most 512 threads
@@ -61,7 +69,10 @@ struct I3 {
     int by_smem = (int)((228 * 1024) / (SMEM + 1024));
     int by_thr = 2048 / THREADS;
     int m = by_smem < by_thr ? by_smem : by_thr;
-    return m < 1 ? 1 : (m > 4 ? 4 : m);
+    // boundary patches: longer lines need more registers; they run beside
+    // the interior kernel
+    const int cap = BND ? 2 : 4;
+    return m < 1 ? 1 : (m > cap ? cap : m);
   }
   static constexpr int MINB = minblocks();
   // vector width (elements) of a contiguous run of NN nodes: 16-byte loads
@@ -105,19 +116,42 @@ __device__ __forceinline__ void i3_st_pairs(T* p, const T (&o)[PO]) {
   }
 }
 
-template <int NN, typename T>
-__global__ void __launch_bounds__(I3<NN, T>::THREADS, I3<NN, T>::MINB)
-    smooth_int3_kernel(const __grid_constant__ SmoothOps<2 * NN - 2, 2 * NN, T, 1> ops, int colour,
-                       const T* __restrict__ b, T* x, int N, int consistent, long long ndofs, PatchGrid grid) {
-  using C = I3<NN, T>;
-  constexpr int P = C::P, PO = C::PO, TPP = C::TPP, PPC = C::PPC, ND = NN * NN * NN;
+// Calls f(std::integral_constant<int, TY>) for the patch's operator type of
+// one direction, so that the body reads that operator set from the kernel
+// parameters at compile-time offsets (constant-bank operands).  The boundary
+// kernel has p^2 = 4n^2 threads per patch, a multiple of 32: the branch is
+// uniform within each warp.
+template <bool BND, class F>
+__device__ __forceinline__ void i3_with_type(int ty, F&& f) {
+  if constexpr (!BND) {
+    f(std::integral_constant<int, 0>{});
+  } else {
+    switch (ty) {
+      case 0: f(std::integral_constant<int, 0>{}); break;
+      case 1: f(std::integral_constant<int, 1>{}); break;
+      case 2: f(std::integral_constant<int, 2>{}); break;
+      default: f(std::integral_constant<int, 3>{}); break;
+    }
+  }
+}
+
+template <int NN, typename T, bool BND>
+__global__ void __launch_bounds__(I3<NN, T, BND>::THREADS, I3<NN, T, BND>::MINB)
+    smooth_int3_kernel(const __grid_constant__ SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT> ops,
+                       int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
+                       PatchGrid grid) {
+  using C = I3<NN, T, BND>;
+  using Ops = Ops1D<C::PO, 2 * NN, T>;
+  constexpr int P = C::P, PO = C::PO, OFF = C::OFF, TPP = C::TPP, PPC = C::PPC, ND = NN * NN * NN;
   constexpr int SA1 = C::SA1, SC = C::SC, CZS = C::CZS, ST = C::ST, SQ = C::SQ;
-  const auto& op = ops.t[0];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* dinv = reinterpret_cast<T*>(smem_raw);  // [k0][k2][k1]
-  for (int e = threadIdx.x; e < C::DINV; e += blockDim.x) {
-    const int k1 = e % PO, k2 = (e / PO) % PO, k0 = e / (PO * PO);
-    dinv[e] = T(1) / (op.lam[k0] + op.lam[k1] + op.lam[k2]);
+  T* dinv = reinterpret_cast<T*>(smem_raw);  // interior: [k0][k2][k1]
+  if (!BND) {
+    const Ops& o0 = ops.t[0];
+    for (int e = threadIdx.x; e < C::DINV; e += blockDim.x) {
+      const int k1 = e % PO, k2 = (e / PO) % PO, k0 = e / (PO * PO);
+      dinv[e] = T(1) / (o0.lam[k0] + o0.lam[k1] + o0.lam[k2]);
+    }
   }
   const int tid = threadIdx.x;
   const int lane = tid % TPP;
@@ -128,11 +162,20 @@ __global__ void __launch_bounds__(I3<NN, T>::THREADS, I3<NN, T>::MINB)
   const long long col = (long long)blockIdx.y * ndofs;
   b += col;
   x += col;
-  const int pidx = blockIdx.x * PPC + pl;
-  const bool valid = pidx < (int)grid.n_int;
-  int v[3];
-  {
-    int q = valid ? pidx : 0;
+  const long long npatch = BND ? grid.n_bnd : grid.n_int;
+  const long long pidx = (long long)blockIdx.x * PPC + pl;
+  const bool valid = pidx < npatch;
+  int v[3], ty[3] = {0, 0, 0};
+  if (BND) {
+    int m[3] = {0, 0, 0};
+    patch_index<3, true>(grid, valid ? pidx : 0, m);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      v[e] = ((colour >> e) & 1) ? 2 * m[e] + 1 : 2 * m[e] + 2;
+      ty[e] = (v[e] == 1 ? 1 : 0) | (v[e] == N - 1 ? 2 : 0);
+    }
+  } else {
+    int q = valid ? (int)pidx : 0;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       const int w = grid.hi[e] - grid.lo[e];
@@ -141,6 +184,14 @@ __global__ void __launch_bounds__(I3<NN, T>::THREADS, I3<NN, T>::MINB)
       v[e] = ((colour >> e) & 1) ? 2 * m + 1 : 2 * m + 2;
     }
   }
+  // face-node halos: the cells across each patch face, when inside the domain
+  bool exlo[3], exhi[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    exlo[e] = consistent && (!BND || v[e] >= 2);
+    exhi[e] = consistent && (!BND || v[e] + 1 <= N - 1);
+  }
+
   // cell (v0-1, v1-1, v2-1), node 0: all patch offsets below are relative to it
   const T* xb = x + ((long long)(v[0] - 1) + (long long)N * ((v[1] - 1) + (long long)N * (v[2] - 1))) * ND;
   const int cs1 = N * ND, cs2 = N * N * ND;  // cell strides in y and z (elements)
@@ -156,7 +207,8 @@ __global__ void __launch_bounds__(I3<NN, T>::THREADS, I3<NN, T>::MINB)
     for (int q = 0; q < R1; ++q) {
       const int t = lane + q * TPP;
       int off = 0;
-      bool act = t < L1, main = t < P * P;
+      const bool act = t < L1, main = t < P * P;
+      bool ld = main;
       if (main) {
         const int a2 = t % P, a1 = t / P;
         off = (a1 / NN) * cs1 + (a2 / NN) * cs2 + (a1 % NN) * NN + (a2 % NN) * NN * NN;
@@ -164,11 +216,13 @@ __global__ void __launch_bounds__(I3<NN, T>::THREADS, I3<NN, T>::MINB)
         const int h = t - P * P, slot = h / P, j = h % P;
         if (slot < 2) {  // y face: cell row v1-2 (node layer n-1) or v1+1 (layer 0); j = a2
           off = (slot ? 2 : -1) * cs1 + (slot ? 0 : (NN - 1) * NN) + (j / NN) * cs2 + (j % NN) * NN * NN;
+          ld = slot ? exhi[1] : exlo[1];
         } else {         // z face: cell layer v2-2 or v2+1; j = a1
           off = (slot == 3 ? 2 : -1) * cs2 + (slot == 3 ? 0 : (NN - 1) * NN * NN) + (j / NN) * cs1 + (j % NN) * NN;
+          ld = slot == 3 ? exhi[2] : exlo[2];
         }
       }
-      if (act && (main || consistent)) {
+      if (ld) {
         i3_ldrun<NN, C::VW>(xb + off, &vin[q][0]);
         i3_ldrun<NN, C::VW>(xb + off + ND, &vin[q][NN]);
       } else {
@@ -176,26 +230,29 @@ __global__ void __launch_bounds__(I3<NN, T>::THREADS, I3<NN, T>::MINB)
         for (int c = 0; c < P; ++c) vin[q][c] = T(0);
       }
       // x halos of a main line: node n-1 of cell v0-2, node 0 of cell v0+1
-      hl[q][0] = (main && consistent) ? __ldg(xb + off - ND + (NN - 1)) : T(0);
-      hl[q][1] = (main && consistent) ? __ldg(xb + off + 2 * ND) : T(0);
+      hl[q][0] = (main && exlo[0]) ? __ldg(xb + off - ND + (NN - 1)) : T(0);
+      hl[q][1] = (main && exhi[0]) ? __ldg(xb + off + 2 * ND) : T(0);
     }
+    i3_with_type<BND>(ty[0], [&](auto tc) {
+      const Ops& ox = ops.t[decltype(tc)::value];
 #pragma unroll
-    for (int q = 0; q < R1; ++q) {
-      const int t = lane + q * TPP;
-      if (t >= L1) continue;
-      // destination row: A/B[a1][a2][.] for main lines, halo[slot][j][.]
-      const int dst = t < P * P ? SA1 * (t / P) + PO * (t % P)
-                                : (2 * P + (t - P * P) / P) * SA1 + PO * ((t - P * P) % P);
-      T oa[PO];
-      T(&vq)[P] = vin[q];
-      mass_rows<PO, P, NN, 1>(op.Mm, vq, oa);
-      i3_st_pairs<PO>(RA + dst, oa);
-      if (t < P * P) {
-        T ob[PO];
-        sipg_rows<PO, P, NN, 1>(op, vq, hl[q][0], hl[q][1], ob);
-        i3_st_pairs<PO>(RA + P * SA1 + dst, ob);
+      for (int q = 0; q < R1; ++q) {
+        const int t = lane + q * TPP;
+        if (t >= L1) continue;
+        // destination row: A/B[a1][a2][.] for main lines, halo[slot][j][.]
+        const int dst = t < P * P ? SA1 * (t / P) + PO * (t % P)
+                                  : (2 * P + (t - P * P) / P) * SA1 + PO * ((t - P * P) % P);
+        T oa[PO];
+        T(&vq)[P] = vin[q];
+        mass_rows<PO, P, NN, OFF>(ox.Mm, vq, oa);
+        i3_st_pairs<PO>(RA + dst, oa);
+        if (t < P * P) {
+          T ob[PO];
+          sipg_rows<PO, P, NN, OFF>(ox, vq, hl[q][0], hl[q][1], ob);
+          i3_st_pairs<PO>(RA + P * SA1 + dst, ob);
+        }
       }
-    }
+    });
   }
   __syncthreads();
 
@@ -209,141 +266,189 @@ __global__ void __launch_bounds__(I3<NN, T>::THREADS, I3<NN, T>::MINB)
   T* Dd = RB + P * SC;
   T* CZ = RB + 2 * P * SC;
   if (valid) {
+    i3_with_type<BND>(ty[1], [&](auto tc) {
+      const Ops& oy = ops.t[decltype(tc)::value];
 #pragma unroll
-    for (int q = 0; q < R2; ++q) {
-      const int t = lane + q * TPP;
-      if (t >= L2) continue;
-      if (t < PO * P) {
-        const int r0 = t % PO, a2 = t / PO;
-        T va[P], vb[P], oc[PO], od[PO];
+      for (int q = 0; q < R2; ++q) {
+        const int t = lane + q * TPP;
+        if (t >= L2) continue;
+        if (t < PO * P) {
+          const int r0 = t % PO, a2 = t / PO;
+          T va[P], vb[P], oc[PO], od[PO];
 #pragma unroll
-        for (int a1 = 0; a1 < P; ++a1) {
-          va[a1] = RA[SA1 * a1 + t];
-          vb[a1] = RA[P * SA1 + SA1 * a1 + t];
+          for (int a1 = 0; a1 < P; ++a1) {
+            va[a1] = RA[SA1 * a1 + t];
+            vb[a1] = RA[P * SA1 + SA1 * a1 + t];
+          }
+          const T h0 = RA[2 * P * SA1 + t], h1 = RA[(2 * P + 1) * SA1 + t];
+          mass_rows<PO, P, NN, OFF>(oy.Mm, va, oc);
+          sipg_rows<PO, P, NN, OFF>(oy, va, h0, h1, od);
+          mass_rows_acc<PO, P, NN, OFF>(oy.Mm, vb, od);
+#pragma unroll
+          for (int r1 = 0; r1 < PO; ++r1) {
+            Cc[SC * a2 + PO * r1 + r0] = oc[r1];
+            Dd[SC * a2 + PO * r1 + r0] = od[r1];
+          }
+        } else {
+          const int h = t - PO * P, r0 = h % PO, side = h / PO;
+          T vz[P], oc[PO];
+#pragma unroll
+          for (int a1 = 0; a1 < P; ++a1) vz[a1] = RA[(2 * P + 2 + side) * SA1 + PO * a1 + r0];
+          mass_rows<PO, P, NN, OFF>(oy.Mm, vz, oc);
+#pragma unroll
+          for (int r1 = 0; r1 < PO; ++r1) CZ[side * CZS + PO * r1 + r0] = oc[r1];
         }
-        const T h0 = RA[2 * P * SA1 + t], h1 = RA[(2 * P + 1) * SA1 + t];
-        mass_rows<PO, P, NN, 1>(op.Mm, va, oc);
-        sipg_rows<PO, P, NN, 1>(op, va, h0, h1, od);
-        mass_rows_acc<PO, P, NN, 1>(op.Mm, vb, od);
-#pragma unroll
-        for (int r1 = 0; r1 < PO; ++r1) {
-          Cc[SC * a2 + PO * r1 + r0] = oc[r1];
-          Dd[SC * a2 + PO * r1 + r0] = od[r1];
-        }
-      } else {
-        const int h = t - PO * P, r0 = h % PO, side = h / PO;
-        T vz[P], oc[PO];
-#pragma unroll
-        for (int a1 = 0; a1 < P; ++a1) vz[a1] = RA[(2 * P + 2 + side) * SA1 + PO * a1 + r0];
-        mass_rows<PO, P, NN, 1>(op.Mm, vz, oc);
-#pragma unroll
-        for (int r1 = 0; r1 < PO; ++r1) CZ[side * CZS + PO * r1 + r0] = oc[r1];
       }
-    }
+    });
   }
   __syncthreads();
 
   // ------------------------------------------------ z sweep, residual, S_z^T
-  // line (r0, r1) = (lane % PO, lane / PO); node (r0+1, r1+1, r2+1)
+  // line (r0, r1) = (lane % PO, lane / PO); patch node (r0, r1, r2) + OFF
   const int r0 = lane % PO, r1 = lane / PO;
-  const int goff = ((r0 + 1) / NN) * ND + ((r1 + 1) / NN) * cs1 + ((r0 + 1) % NN) + ((r1 + 1) % NN) * NN;
+  const int goff = ((r0 + OFF) / NN) * ND + ((r1 + OFF) / NN) * cs1 + ((r0 + OFF) % NN) + ((r1 + OFF) % NN) * NN;
   T* gx = const_cast<T*>(xb) + goff;
   const T* gb = b + (xb - x) + goff;
+  // rows of V_j (all rows for interior patches): [first, last] per direction
+  int zlo = 0, zhi = PO - 1;
+  bool inxy = true;
+  if (BND) {
+    const Ops& fx = ops.t[ty[0]];
+    const Ops& fy = ops.t[ty[1]];
+    const Ops& fz = ops.t[ty[2]];
+    inxy = r0 >= fx.first && r0 <= fx.last && r1 >= fy.first && r1 <= fy.last;
+    zlo = fz.first;
+    zhi = fz.last;
+  }
   if (valid) {
-    T bv[PO], vc[P], vd[P], o[PO], t1[PO];
+    i3_with_type<BND>(ty[2], [&](auto tc) {
+      const Ops& oz = ops.t[decltype(tc)::value];
+      T bv[PO], vc[P], vd[P], o[PO], t1[PO];
 #pragma unroll
-    for (int r2 = 0; r2 < PO; ++r2)
-      bv[r2] = __ldg(gb + ((r2 + 1) / NN) * cs2 + ((r2 + 1) % NN) * NN * NN);
+      for (int r2 = 0; r2 < PO; ++r2) {
+        const bool in = inxy && r2 >= zlo && r2 <= zhi;
+        bv[r2] = in ? __ldg(gb + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN) : T(0);
+      }
 #pragma unroll
-    for (int a2 = 0; a2 < P; ++a2) {
-      vc[a2] = Cc[SC * a2 + lane];
-      vd[a2] = Dd[SC * a2 + lane];
-    }
-    sipg_rows<PO, P, NN, 1>(op, vc, CZ[lane], CZ[CZS + lane], o);
-    mass_rows_acc<PO, P, NN, 1>(op.Mm, vd, o);
+      for (int a2 = 0; a2 < P; ++a2) {
+        vc[a2] = Cc[SC * a2 + lane];
+        vd[a2] = Dd[SC * a2 + lane];
+      }
+      sipg_rows<PO, P, NN, OFF>(oz, vc, CZ[lane], CZ[CZS + lane], o);
+      mass_rows_acc<PO, P, NN, OFF>(oz.Mm, vd, o);
 #pragma unroll
-    for (int r2 = 0; r2 < PO; ++r2) o[r2] = bv[r2] - o[r2];
-    st_rows<PO>(op.S, o, t1);
+      for (int r2 = 0; r2 < PO; ++r2) {
+        const bool in = inxy && r2 >= zlo && r2 <= zhi;
+        o[r2] = in ? bv[r2] - o[r2] : T(0);
+      }
+      st_rows<PO>(oz.S, o, t1);
 #pragma unroll
-    for (int k2 = 0; k2 < PO; ++k2) RA[ST * r1 + PO * k2 + r0] = t1[k2];
+      for (int k2 = 0; k2 < PO; ++k2) RA[ST * r1 + PO * k2 + r0] = t1[k2];
+    });
   }
   __syncthreads();
 
   // ------------------------------------------------------------- S_y^T
   // line (r0, k2) = (lane % PO, lane / PO)
   if (valid) {
-    T w[PO], o[PO];
+    i3_with_type<BND>(ty[1], [&](auto tc) {
+      const Ops& oy = ops.t[decltype(tc)::value];
+      T w[PO], o[PO];
 #pragma unroll
-    for (int j = 0; j < PO; ++j) w[j] = RA[ST * j + lane];
-    st_rows<PO>(op.S, w, o);
+      for (int j = 0; j < PO; ++j) w[j] = RA[ST * j + lane];
+      st_rows<PO>(oy.S, w, o);
 #pragma unroll
-    for (int k1 = 0; k1 < PO; ++k1) RB[SQ * r0 + PO * r1 + k1] = o[k1];  // r1 here = k2
+      for (int k1 = 0; k1 < PO; ++k1) RB[SQ * r0 + PO * r1 + k1] = o[k1];  // r1 here = k2
+    });
   }
   __syncthreads();
 
   // ------------------------------------ S_x^T, Lambda^{-1}, S_x  (line (k1, k2))
   if (valid) {
-    T w[PO], o[PO];
+    // lambda_y(k1) + lambda_z(k2), (k1, k2) = (r0, r1)
+    const T lyz = BND ? ops.t[ty[1]].lam[r0] + ops.t[ty[2]].lam[r1] : T(0);
+    i3_with_type<BND>(ty[0], [&](auto tc) {
+      const Ops& ox = ops.t[decltype(tc)::value];
+      T w[PO], o[PO];
 #pragma unroll
-    for (int j = 0; j < PO; ++j) w[j] = RB[SQ * j + lane];
-    st_rows<PO>(op.S, w, o);
+      for (int j = 0; j < PO; ++j) w[j] = RB[SQ * j + lane];
+      st_rows<PO>(ox.S, w, o);
+      if (BND) {
 #pragma unroll
-    for (int k0 = 0; k0 < PO; ++k0) o[k0] *= dinv[k0 * PO * PO + lane];
-    s_rows<PO>(op.S, o, w);
+        for (int k0 = 0; k0 < PO; ++k0) o[k0] = o[k0] / (ox.lam[k0] + lyz);
+      } else {
 #pragma unroll
-    for (int j = 0; j < PO; ++j) RA[SQ * r0 + PO * r1 + j] = w[j];  // (k1, k2) = (r0, r1)
+        for (int k0 = 0; k0 < PO; ++k0) o[k0] *= dinv[k0 * PO * PO + lane];
+      }
+      s_rows<PO>(ox.S, o, w);
+#pragma unroll
+      for (int j = 0; j < PO; ++j) RA[SQ * r0 + PO * r1 + j] = w[j];
+    });
   }
   __syncthreads();
 
   // ------------------------------------------------------------- S_y  (line (r0, k2))
   if (valid) {
-    T w[PO], o[PO];
+    i3_with_type<BND>(ty[1], [&](auto tc) {
+      const Ops& oy = ops.t[decltype(tc)::value];
+      T w[PO], o[PO];
 #pragma unroll
-    for (int j = 0; j < PO; ++j) w[j] = RA[SQ * j + lane];
-    s_rows<PO>(op.S, w, o);
+      for (int j = 0; j < PO; ++j) w[j] = RA[SQ * j + lane];
+      s_rows<PO>(oy.S, w, o);
 #pragma unroll
-    for (int j = 0; j < PO; ++j) RB[ST * j + lane] = o[j];
+      for (int j = 0; j < PO; ++j) RB[ST * j + lane] = o[j];
+    });
   }
   __syncthreads();
 
   // ------------------------------------------------- S_z, x += u  (line (r0, r1))
   if (valid) {
-    T w[PO], o[PO], xo[PO];
+    i3_with_type<BND>(ty[2], [&](auto tc) {
+      const Ops& oz = ops.t[decltype(tc)::value];
+      T w[PO], o[PO], xo[PO];
 #pragma unroll
-    for (int r2 = 0; r2 < PO; ++r2) xo[r2] = gx[((r2 + 1) / NN) * cs2 + ((r2 + 1) % NN) * NN * NN];
+      for (int r2 = 0; r2 < PO; ++r2) {
+        const bool in = inxy && r2 >= zlo && r2 <= zhi;
+        xo[r2] = in ? gx[((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN] : T(0);
+      }
 #pragma unroll
-    for (int k2 = 0; k2 < PO; ++k2) w[k2] = RB[ST * r1 + PO * k2 + r0];
-    s_rows<PO>(op.S, w, o);
+      for (int k2 = 0; k2 < PO; ++k2) w[k2] = RB[ST * r1 + PO * k2 + r0];
+      s_rows<PO>(oz.S, w, o);
 #pragma unroll
-    for (int r2 = 0; r2 < PO; ++r2) gx[((r2 + 1) / NN) * cs2 + ((r2 + 1) % NN) * NN * NN] = xo[r2] + o[r2];
+      for (int r2 = 0; r2 < PO; ++r2) {
+        const bool in = inxy && r2 >= zlo && r2 <= zhi;
+        if (in) gx[((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN] = xo[r2] + o[r2];
+      }
+    });
   }
 }
 
-template <int NN, typename T>
+template <int NN, typename T, bool BND>
 cudaError_t launch_int3(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
                         cudaStream_t s) {
-  using C = I3<NN, T>;
+  using C = I3<NN, T, BND>;
+  const long long np = BND ? g.n_bnd : g.n_int;
+  if (np <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(smooth_int3_kernel<NN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(smooth_int3_kernel<NN, T, BND>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  SmoothOps<C::PO, C::P, T, 1> ops;
-  make_ops<C::PO, C::P, false, T>(h->hcst<T>(level), 0, ops.t[0]);
-  dim3 grid((unsigned)((g.n_int + C::PPC - 1) / C::PPC), h->prm.nrhs);
-  smooth_int3_kernel<NN, T><<<grid, C::THREADS, C::SMEM, s>>>(
+  SmoothOps<C::PO, C::P, T, C::NT> ops;
+  for (int t = 0; t < C::NT; ++t) make_ops<C::PO, C::P, BND, T>(h->hcst<T>(level), t, ops.t[t]);
+  dim3 grid((unsigned)((np + C::PPC - 1) / C::PPC), h->prm.nrhs);
+  smooth_int3_kernel<NN, T, BND><<<grid, C::THREADS, C::SMEM, s>>>(
       ops, colour, b, x, h->lv[level].N, h->prm.smoother == SIPG_SMOOTHER_CONSISTENT ? 1 : 0,
       (long long)h->lv[level].ndofs, g);
   return cudaGetLastError();
 }
 
-// The register-direct kernel takes the interior patches of 3D FP32 colour
-// passes: its vector loads need 16-byte aligned vectors, and patch indices
-// are 32-bit.
+// The register-direct kernels take the 3D FP32 colour passes: their vector
+// loads need 16-byte aligned vectors, and interior patch indices are 32-bit.
 template <int DIM, typename T>
 bool use_int3(const PatchGrid& g, const void* b, const void* x) {
-  return DIM == 3 && sizeof(T) == 4 && g.n_int > 0 && g.n_int < (1LL << 31) &&
-         (reinterpret_cast<uintptr_t>(b) % 16) == 0 && (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+  return DIM == 3 && sizeof(T) == 4 && g.n_int < (1LL << 31) && (reinterpret_cast<uintptr_t>(b) % 16) == 0 &&
+         (reinterpret_cast<uintptr_t>(x) % 16) == 0;
 }

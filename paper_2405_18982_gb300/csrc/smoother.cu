@@ -29,6 +29,7 @@
 // have zero operators, the eigenvectors are padded by the identity and their
 // residual is zeroed, so the update is exactly the local solve on V_j.
 #include <algorithm>
+#include <type_traits>
 
 #include "tensor_ops.cuh"
 
@@ -756,12 +757,12 @@ PatchGrid make_grid(int dim, int N, int colour);
 
 #include "smooth_int3.cuh"
 
-template <int DIM, int NN, typename T>
-cudaError_t launch_interior(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
-                            cudaStream_t s) {
+template <int DIM, int NN, bool BND, typename T>
+cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
+                           cudaStream_t s) {
   if constexpr (DIM == 3 && sizeof(T) == 4)
-    if (use_int3<DIM, T>(g, b, x)) return launch_int3<NN, T>(h, level, colour, b, x, g, s);
-  return launch_part<DIM, NN, false, T>(h, level, colour, b, x, g, s);
+    if (use_int3<DIM, T>(g, b, x)) return launch_int3<NN, T, BND>(h, level, colour, b, x, g, s);
+  return launch_part<DIM, NN, BND, T>(h, level, colour, b, x, g, s);
 }
 
 template <typename T, int DIM, int NN>
@@ -775,14 +776,14 @@ cudaError_t smooth_dispatch2(const sipg_handle* h, int level, int colour, const 
     // its CTAs fill the SMs the interior grid leaves idle in its last wave
     if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    if ((e = launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, h->side)) != cudaSuccess) return e;
-    if ((e = launch_interior<DIM, NN, T>(h, level, colour, b, x, g, s)) != cudaSuccess) return e;
+    if ((e = launch_patches<DIM, NN, true, T>(h, level, colour, b, x, g, h->side)) != cudaSuccess) return e;
+    if ((e = launch_patches<DIM, NN, false, T>(h, level, colour, b, x, g, s)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     return cudaStreamWaitEvent(s, h->ev_join, 0);
   }
-  e = launch_interior<DIM, NN, T>(h, level, colour, b, x, g, s);
+  e = launch_patches<DIM, NN, false, T>(h, level, colour, b, x, g, s);
   if (e != cudaSuccess) return e;
-  return launch_part<DIM, NN, true, T>(h, level, colour, b, x, g, s);
+  return launch_patches<DIM, NN, true, T>(h, level, colour, b, x, g, s);
 }
 
 // ------------------------------------------------------------------ fused step
