@@ -72,6 +72,13 @@ sipg_status vcycle_T(sipg_handle* h, const T* bL, T* xL, cudaStream_t s) {
     SIPG_CHECK(cudaMemsetAsync(x, 0, h->lv[l].ndofs * nr * sizeof(T), s), "memset");
     sipg_status st = smooth_T<T>(h, l, 0, b, x, s);
     if (st) return st;
+    cudaError_t e = launch_residual_restrict<T>(h, l, b, x, bvec(l - 1), s);
+    if (e == cudaSuccess) {
+      h->launches += 1;
+      continue;
+    }
+    if (e != cudaErrorNotSupported) return cuda_fail(h, e, "residual and restriction");
+    cudaGetLastError();
     T* r = reinterpret_cast<T*>(h->vr(l));
     SIPG_CHECK(launch_apply<T>(h, l, APPLY_RESIDUAL, b, x, r, s), "residual");
     SIPG_CHECK(launch_restrict<T>(h, l, r, bvec(l - 1), s), "restrict");

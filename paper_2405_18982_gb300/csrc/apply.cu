@@ -248,6 +248,13 @@ cudaError_t manufactured_dispatch2(const sipg_handle* h, double* f, cudaStream_t
   return cudaGetLastError();
 }
 
+#include "apply3.cuh"
+
+template <int NN, typename T>
+cudaError_t apply3_try(const sipg_handle* h, int level, int mode, const T* b, const T* x, T* y, cudaStream_t s) {
+  return launch_apply3<NN, T>(h, level, mode, b, x, y, s);
+}
+
 }  // namespace
 
 #define SIPG_DISPATCH_N(FN, DIM, ...)                                  \
@@ -289,11 +296,47 @@ static cudaError_t apply_dim(const sipg_handle* h, int level, int mode, const T*
   return cudaErrorInvalidValue;
 }
 
+// The coarse-cell-organised 3D kernel where it applies (FP32, 16-byte
+// aligned vectors, N even with whole CTA groups), else the cell-block kernel.
+// FP64 stays on the cell-block kernel: bound by the FP64 pipe, it is faster
+// there (1.39 ms against 1.53 ms for 16.8M DoFs, Q3).
+template <typename T>
+static cudaError_t apply3_dim(const sipg_handle* h, int level, int mode, const T* b, const T* x, T* y,
+                              cudaStream_t s) {
+  if (h->prm.dim != 3 || sizeof(T) != 4) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(y)) % 16)
+    return cudaErrorNotSupported;
+  switch (h->n) {
+    case 2: return apply3_try<2, T>(h, level, mode, b, x, y, s);
+    case 3: return apply3_try<3, T>(h, level, mode, b, x, y, s);
+    case 4: return apply3_try<4, T>(h, level, mode, b, x, y, s);
+    case 5: return apply3_try<5, T>(h, level, mode, b, x, y, s);
+    case 6: return apply3_try<6, T>(h, level, mode, b, x, y, s);
+    case 7: return apply3_try<7, T>(h, level, mode, b, x, y, s);
+    case 8: return apply3_try<8, T>(h, level, mode, b, x, y, s);
+  }
+  return cudaErrorNotSupported;
+}
+
 template <typename T>
 cudaError_t launch_apply(const sipg_handle* h, int level, int mode, const T* b, const T* x, T* y,
                          cudaStream_t s) {
+  if (mode == APPLY_Y || mode == APPLY_RESIDUAL) {
+    cudaError_t e = apply3_dim<T>(h, level, mode == APPLY_Y ? A3_APPLY : A3_RESIDUAL, b, x, y, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   return apply_dim<T>(h, level, mode, b, x, y, s);
 }
+
+template <typename T>
+cudaError_t launch_residual_restrict(const sipg_handle* h, int level, const T* b, const T* x, T* rc,
+                                     cudaStream_t s) {
+  return apply3_dim<T>(h, level, A3_RESTRICT, b, x, rc, s);
+}
+template cudaError_t launch_residual_restrict<double>(const sipg_handle*, int, const double*, const double*,
+                                                      double*, cudaStream_t);
+template cudaError_t launch_residual_restrict<float>(const sipg_handle*, int, const float*, const float*, float*,
+                                                     cudaStream_t);
 template cudaError_t launch_apply<double>(const sipg_handle*, int, int, const double*, const double*,
                                           double*, cudaStream_t);
 template cudaError_t launch_apply<float>(const sipg_handle*, int, int, const float*, const float*,

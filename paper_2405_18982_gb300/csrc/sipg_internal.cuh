@@ -156,6 +156,11 @@ cudaError_t launch_restrict(const sipg_handle* h, int fine_level, const T* rf, T
 template <typename T>
 cudaError_t launch_prolongate_add(const sipg_handle* h, int fine_level, const T* ec, T* xf,
                                   cudaStream_t s);
+// b_{level-1} = P^T (b - A x) on `level` without storing the fine residual;
+// cudaErrorNotSupported where the fused kernel does not apply.
+template <typename T>
+cudaError_t launch_residual_restrict(const sipg_handle* h, int level, const T* b, const T* x, T* rc,
+                                     cudaStream_t s);
 template <typename T>
 cudaError_t launch_coarse_solve(const sipg_handle* h, const T* b0, T* x0, cudaStream_t s);
 

@@ -28,13 +28,6 @@
 // memory, rows outside V_j with zero operators, S padded by the identity, the
 // residual zeroed outside V_j and halos outside the domain read as zero.
 
-constexpr int i3_pad32(int m, int r) {
-  int s = m;
-  while (((s % 32) + 32) % 32 != ((r % 32) + 32) % 32) ++s;
-  return s;
-}
-constexpr int i3_max(int a, int b) { return a > b ? a : b; }
-
 template <int NN, typename T, bool BND>
 struct I3 {
   static constexpr int P = 2 * NN;                      // patch nodes per direction
@@ -75,33 +68,8 @@ struct I3 {
     return m < 1 ? 1 : (m > cap ? cap : m);
   }
   static constexpr int MINB = minblocks();
-  // vector width (elements) of a contiguous run of NN nodes: 16-byte loads
-  // when the run is 16-byte aligned, else 8-byte, else scalar
-  static constexpr int VW = (NN * (int)sizeof(T)) % 16 == 0 ? 16 / (int)sizeof(T)
-                            : ((NN * (int)sizeof(T)) % 8 == 0 ? 8 / (int)sizeof(T) : 1);
+  static constexpr int VW = run_vw<NN, T>();
 };
-
-template <typename T, int V>
-struct i3_vec;
-template <> struct i3_vec<float, 4> { using t = float4; };
-template <> struct i3_vec<float, 2> { using t = float2; };
-template <> struct i3_vec<float, 1> { using t = float; };
-template <> struct i3_vec<double, 2> { using t = double2; };
-template <> struct i3_vec<double, 1> { using t = double; };
-
-// v[0..NN) = p[0..NN) through the read-only path (vector loads of width VW)
-template <int NN, int VW, typename T>
-__device__ __forceinline__ void i3_ldrun(const T* __restrict__ p, T* v) {
-  using V = typename i3_vec<T, VW>::t;
-  const V* q = reinterpret_cast<const V*>(p);
-#pragma unroll
-  for (int j = 0; j < NN / VW; ++j) {
-    const V w = __ldg(q + j);
-    const T* e = reinterpret_cast<const T*>(&w);
-#pragma unroll
-    for (int c = 0; c < VW; ++c) v[j * VW + c] = e[c];
-  }
-}
 
 // store PO consecutive values as pairs (PO is even)
 template <int PO, typename T>

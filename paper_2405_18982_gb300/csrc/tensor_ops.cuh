@@ -54,3 +54,44 @@ __device__ __forceinline__ void copy_block(T* __restrict__ dst, const T (*src)[S
                                            int nthreads) {
   for (int e = tid; e < NN * NN; e += nthreads) dst[e] = src[e / NN][e % NN];
 }
+
+// Smallest s >= m with s = r (mod 32): strides that place the lines of a
+// shared-memory tile on chosen banks.
+constexpr int i3_pad32(int m, int r) {
+  int s = m;
+  while (((s % 32) + 32) % 32 != ((r % 32) + 32) % 32) ++s;
+  return s;
+}
+constexpr int i3_max(int a, int b) { return a > b ? a : b; }
+
+// Vector width (elements) for loading a contiguous run of NN nodes of a
+// cell-wise vector: 16-byte loads when every run is 16-byte aligned, else
+// 8-byte, else scalar.
+template <int NN, typename T>
+constexpr int run_vw() {
+  return (NN * (int)sizeof(T)) % 16 == 0 ? 16 / (int)sizeof(T)
+                                         : ((NN * (int)sizeof(T)) % 8 == 0 ? 8 / (int)sizeof(T) : 1);
+}
+
+template <typename T, int V>
+struct i3_vec;
+template <> struct i3_vec<float, 4> { using t = float4; };
+template <> struct i3_vec<float, 2> { using t = float2; };
+template <> struct i3_vec<float, 1> { using t = float; };
+template <> struct i3_vec<double, 2> { using t = double2; };
+template <> struct i3_vec<double, 1> { using t = double; };
+
+// v[0..NN) = p[0..NN) through the read-only path (vector loads of width VW)
+template <int NN, int VW, typename T>
+__device__ __forceinline__ void i3_ldrun(const T* __restrict__ p, T* v) {
+  using V = typename i3_vec<T, VW>::t;
+  const V* q = reinterpret_cast<const V*>(p);
+#pragma unroll
+  for (int j = 0; j < NN / VW; ++j) {
+    const V w = __ldg(q + j);
+    const T* e = reinterpret_cast<const T*>(&w);
+#pragma unroll
+    for (int c = 0; c < VW; ++c) v[j * VW + c] = e[c];
+  }
+}
+
