@@ -7,6 +7,7 @@ the Python side loads it with ctypes.
 """
 import concurrent.futures as cf
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -15,9 +16,14 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
-BUILD_DIR = os.path.join(PKG, "_build")
+# objects per host architecture: a tree copied between an x86 and an Arm
+# machine never reuses the other's objects
+BUILD_DIR = os.path.join(PKG, "_build", platform.machine())
 LIB = os.path.join(OUT_DIR, "libsipg.so")
-SOURCES = ["api.cu", "setup.cu", "apply.cu", "smoother.cu", "transfer.cu", "krylov.cu", "noalloc.cu"]
+STAMP = os.path.join(OUT_DIR, "libsipg.machine")
+# the colour-pass instantiation units are the slowest: they go first
+SOURCES = (sorted(f for f in os.listdir(CSRC) if f.startswith("smooth_i_") and f.endswith(".cu")) +
+           ["apply.cu", "setup.cu", "transfer.cu", "smoother.cu", "api.cu", "krylov.cu", "noalloc.cu"])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,10 +47,19 @@ def cuda_lib_dir():
     return os.path.join(home, "lib64")
 
 
-def _compile(src, verbose):
+def _headers_mtime():
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    hdrs += [os.path.join(ROOT, "include", "sipg.h"), os.path.abspath(__file__)]
+    return max(os.path.getmtime(h) for h in hdrs)
+
+
+def _compile(src, verbose, force):
     obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
+    if (not verbose and not force and os.path.exists(obj) and
+            os.path.getmtime(obj) >= max(os.path.getmtime(os.path.join(CSRC, src)), _headers_mtime())):
+        return obj, ""  # object newer than its source and every header
     cmd = [nvcc_path(), "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17",
-           "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+           "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-diag-suppress", "177",
            "-I", os.path.join(ROOT, "include")] + ARCH
     if verbose:
         cmd += ["-Xptxas", "-v"]
@@ -55,8 +70,11 @@ def _compile(src, verbose):
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
+    with open(STAMP) as fh:
+        if fh.read().strip() != platform.machine():
+            return False
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "sipg.h"),
                                                                    os.path.abspath(__file__)]
@@ -71,7 +89,7 @@ def build(force=False, verbose=False, jobs=None):
     os.makedirs(OUT_DIR, exist_ok=True)
     jobs = jobs or min(len(SOURCES), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, verbose, force), SOURCES))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
@@ -84,6 +102,8 @@ def build(force=False, verbose=False, jobs=None):
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(platform.machine() + "\n")
     return LIB
 
 

@@ -303,19 +303,23 @@ static cudaError_t apply_dim(const sipg_handle* h, int level, int mode, const T*
 template <typename T>
 static cudaError_t apply3_dim(const sipg_handle* h, int level, int mode, const T* b, const T* x, T* y,
                               cudaStream_t s) {
-  if (h->prm.dim != 3 || sizeof(T) != 4) return cudaErrorNotSupported;
-  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(y)) % 16)
+  if constexpr (sizeof(T) != 4) {
     return cudaErrorNotSupported;
-  switch (h->n) {
-    case 2: return apply3_try<2, T>(h, level, mode, b, x, y, s);
-    case 3: return apply3_try<3, T>(h, level, mode, b, x, y, s);
-    case 4: return apply3_try<4, T>(h, level, mode, b, x, y, s);
-    case 5: return apply3_try<5, T>(h, level, mode, b, x, y, s);
-    case 6: return apply3_try<6, T>(h, level, mode, b, x, y, s);
-    case 7: return apply3_try<7, T>(h, level, mode, b, x, y, s);
-    case 8: return apply3_try<8, T>(h, level, mode, b, x, y, s);
+  } else {
+    if (h->prm.dim != 3) return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(y)) % 16)
+      return cudaErrorNotSupported;
+    switch (h->n) {
+      case 2: return apply3_try<2, T>(h, level, mode, b, x, y, s);
+      case 3: return apply3_try<3, T>(h, level, mode, b, x, y, s);
+      case 4: return apply3_try<4, T>(h, level, mode, b, x, y, s);
+      case 5: return apply3_try<5, T>(h, level, mode, b, x, y, s);
+      case 6: return apply3_try<6, T>(h, level, mode, b, x, y, s);
+      case 7: return apply3_try<7, T>(h, level, mode, b, x, y, s);
+      case 8: return apply3_try<8, T>(h, level, mode, b, x, y, s);
+    }
+    return cudaErrorNotSupported;
   }
-  return cudaErrorNotSupported;
 }
 
 template <typename T>

@@ -1,0 +1,8 @@
+// Explicit instantiations of the colour-pass and fused-step kernels:
+// 2D, float, n = 2, 3, 4 (split across translation units so
+// that they compile in parallel).
+#include "smoother_impl.cuh"
+
+SIPG_SMOOTH_INST(2, float, 2)
+SIPG_SMOOTH_INST(2, float, 3)
+SIPG_SMOOTH_INST(2, float, 4)

@@ -1,0 +1,7 @@
+// Explicit instantiations of the colour-pass and fused-step kernels:
+// 2D, double, n = 5, 6 (split across translation units so
+// that they compile in parallel).
+#include "smoother_impl.cuh"
+
+SIPG_SMOOTH_INST(2, double, 5)
+SIPG_SMOOTH_INST(2, double, 6)

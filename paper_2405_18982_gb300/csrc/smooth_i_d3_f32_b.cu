@@ -1,0 +1,7 @@
+// Explicit instantiations of the colour-pass and fused-step kernels:
+// 3D, float, n = 5, 6 (split across translation units so
+// that they compile in parallel).
+#include "smoother_impl.cuh"
+
+SIPG_SMOOTH_INST(3, float, 5)
+SIPG_SMOOTH_INST(3, float, 6)
