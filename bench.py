@@ -44,6 +44,11 @@ WORKLOAD = ("3D SIPG Poisson, unit cube, 64^3 cells, 6 levels, Q3 GLL (16.8M DoF
             "gamma = 2k(k+1)/h, f = manufactured 3pi^2 prod sin + U[-1,1] noise (seed 2), "
             "FP32 V-cycle (1+1 vertex-patch smoothing) inside FP64 flexible CG to 1e-10; "
             "plain FP64 solve timed beside it")
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
+# capture of this kernel (summary under profiles/); None when
+# the kernel has changed since that capture
+TRAFFIC_INTERIOR_COLOUR0 = 141064960  # 127.02 MB read + 14.04 MB written
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
 # peaks (MEASURED_PEAKS.json for HBM; ALU peaks from unit counts x max SM clock)
 SMS, FP32_LANES, FP64_UNITS, SM_MAX_MHZ = 152, 128, 2, 2070.0
 
@@ -81,7 +86,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -269,28 +274,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_vc64 = ev0.elapsed_time(ev1) / 1e3 / 3
 
-    # ---- dominant kernel: finest-level FP32 colour pass, timed per launch
+    # ---- dominant kernel: the finest-level FP32 interior colour pass.  Colour
+    # 0 (all vertex indices even) has no patch on the domain boundary, so
+    # sipg_smooth_colour launches exactly one kernel (smooth_int3_kernel<4,
+    # float, interior>) on the calling stream; CUDA events around repeated
+    # launches give its average duration.
     L = NLEV - 1
     N = 1 << LOG2N
-    nrep = 5
-    col_t = []
-    for c in range(2 ** DIM):
-        s_mix.smooth_colour(L, c, bf, xf)
+    nrep = 20
+    for _ in range(3):
+        s_mix.smooth_colour(L, 0, bf, xf)
     torch.cuda.synchronize()
-    tot_fl = tot_by = 0
     ev0.record(stream)
     for _ in range(nrep):
-        for c in range(2 ** DIM):
-            s_mix.smooth_colour(L, c, bf, xf)
+        s_mix.smooth_colour(L, 0, bf, xf)
     ev1.record(stream)
     torch.cuda.synchronize()
-    t_col = ev0.elapsed_time(ev1) / 1e3 / (nrep * 2 ** DIM)
-    for c in range(2 ** DIM):
-        fl, by, _ = smoother_counts(DIM, K, N, c, 4)
-        tot_fl += fl
-        tot_by += by
-    fl_launch = tot_fl / 2 ** DIM
-    by_launch = tot_by / 2 ** DIM
+    t_col = ev0.elapsed_time(ev1) / 1e3 / nrep
+    fl_launch, by_launch, npatch0 = smoother_counts(DIM, K, N, 0, 4)
     hbm, hbm_src = measured_peaks()
     achieved_tf = fl_launch / t_col / 1e12
     achieved_gb = by_launch / t_col / 1e9
@@ -304,8 +305,9 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": round(achieved_gb, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(frac_hbm, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
-    roof.update({"kernel": "smooth_colour_kernel<3,4,float> (finest level, one colour pass)",
-                 "traffic": None, "avg_launch_us": round(t_col * 1e6, 2),
+    roof.update({"kernel": "smooth_int3_kernel<4,float,interior> (finest level, colour 0, %d patches)" % npatch0,
+                 "traffic": TRAFFIC_INTERIOR_COLOUR0, "traffic_source": TRAFFIC_SOURCE,
+                 "avg_launch_us": round(t_col * 1e6, 2),
                  "algorithmic_flops_per_launch": int(fl_launch), "algorithmic_bytes_per_launch": int(by_launch),
                  "hbm_frac": round(frac_hbm, 4), "alu_frac": round(frac_alu, 4)})
 
@@ -513,6 +515,64 @@ def run_batched(args):
                       "single_MDoF_per_s": round(nd / ms_1 / 1e3, 1), "single_iterations": inf1.iterations}))
 
 
+# ----------------------------------------------------------------- throughput sweep
+def run_sweep(args):
+    """--mode sweep: MDoF/s of the finest-level apply, one smoothing step, one
+    V-cycle (FP32) and one mixed solve to 1e-10, over 3D k = 2..7 with
+    N = 16, 32, 64 and 2D k = 2..7 with N = 512, 1024, 2048 (coarsest level 2
+    cells per direction; f ~ N(0,1), seed 3).  One JSON line per configuration."""
+    import torch
+    import paper_2405_18982_gb300 as pkg
+    from paper_2405_18982_gb300 import SIPG, SIPG_FP32, Params, inputs
+    pkg.load(pkg.build())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    cases = [(3, k, l2) for l2 in (4, 5, 6) for k in range(2, 8)] + \
+            [(2, k, l2) for l2 in (9, 10, 11) for k in range(2, 8)]
+    for dim, k, l2 in cases:
+        nd = (1 << l2) ** dim * (k + 1) ** dim
+        if nd > 140_000_000:
+            continue
+        s = SIPG(Params(dim=dim, degree=k, log2_cells=l2, n_levels=l2, vcycle_precision=SIPG_FP32, use_graphs=1))
+        n = s.ndofs()
+        f = torch.from_numpy(inputs.normal(3, n)).to("cuda").view(1, n)
+        b = torch.zeros_like(f)
+        s.rhs(f, b)
+        bf = b.float()
+        xf = torch.zeros_like(bf)
+        yf = torch.zeros_like(bf)
+        x = torch.zeros_like(b)
+        t_apply = timed(lambda: s.apply(l2 - 1, bf, yf), 10)
+        t_smooth = timed(lambda: s.smooth(l2 - 1, bf, xf), 5)
+        t_vc = timed(lambda: s.vcycle(bf, xf), 5)
+
+        def solve():
+            x.zero_()
+            return s.solve(b, x, rtol=1e-10, maxit=200)
+
+        info = solve()
+        t_solve = timed(solve, 2)
+        print(json.dumps({"mode": "sweep", "dim": dim, "degree": k, "cells_per_dir": 1 << l2, "dofs": n,
+                          "apply_fp32_mdofs": round(n / t_apply / 1e6, 1),
+                          "smooth_step_fp32_mdofs": round(n / t_smooth / 1e6, 1),
+                          "vcycle_fp32_mdofs": round(n / t_vc / 1e6, 1),
+                          "solve_mixed_ms": round(t_solve * 1e3, 2), "iterations": info.iterations,
+                          "solve_mdofs_per_vcycle": round(n * info.iterations / t_solve / 1e6, 1)}), flush=True)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+
 # ----------------------------------------------------------------- oracle arm
 SAMPLE = (3, 3, 8, 3)   # dim, k, N, levels: the same discretisation on 8^3 cells
 
@@ -590,13 +650,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode in ("ragged", "multirhs"):
         run_batched(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
     elif args.mode != "solve":
         run_kernel_only(args)
     else:

@@ -103,36 +103,41 @@ __device__ __forceinline__ void i3_with_type(int ty, F&& f) {
   }
 }
 
-template <int NN, typename T, bool BND>
-__global__ void __launch_bounds__(I3<NN, T, BND>::THREADS, I3<NN, T, BND>::MINB)
-    smooth_int3_kernel(const __grid_constant__ SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT> ops,
-                       int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
-                       PatchGrid grid) {
+// Interior table 1 / (lambda_k0 + lambda_k1 + lambda_k2), layout [k0][k2][k1].
+template <int NN, typename T>
+__device__ __forceinline__ void int3_dinv(const Ops1D<2 * NN - 2, 2 * NN, T>& o0, T* dinv) {
+  constexpr int PO = 2 * NN - 2;
+  for (int e = threadIdx.x; e < PO * PO * PO; e += blockDim.x) {
+    const int k1 = e % PO, k2 = (e / PO) % PO, k0 = e / (PO * PO);
+    dinv[e] = T(1) / (o0.lam[k0] + o0.lam[k1] + o0.lam[k2]);
+  }
+}
+
+// Patches pbase + slot (slot < PPC, TPP threads each) of one colour.  Every
+// thread of the CTA calls this (it holds CTA barriers); b and x point at the
+// right-hand side's column; buf holds PPC patch buffers of I3::PS elements;
+// dinv (interior) as written by int3_dinv.  NC: x is read through the
+// read-only (non-coherent) path, valid when no other CTA writes what this
+// launch reads (one colour per launch); the fused step, whose later colours
+// read what other CTAs wrote, uses coherent loads.
+template <int NN, typename T, bool BND, int PPC, bool NC>
+__device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT>& ops,
+                                          const T* dinv, T* buf, long long pbase, int colour,
+                                          const T* __restrict__ b, T* x, int N, int consistent,
+                                          const PatchGrid& grid) {
   using C = I3<NN, T, BND>;
   using Ops = Ops1D<C::PO, 2 * NN, T>;
-  constexpr int P = C::P, PO = C::PO, OFF = C::OFF, TPP = C::TPP, PPC = C::PPC, ND = NN * NN * NN;
+  constexpr int P = C::P, PO = C::PO, OFF = C::OFF, TPP = C::TPP, ND = NN * NN * NN;
   constexpr int SA1 = C::SA1, SC = C::SC, CZS = C::CZS, ST = C::ST, SQ = C::SQ;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* dinv = reinterpret_cast<T*>(smem_raw);  // interior: [k0][k2][k1]
-  if (!BND) {
-    const Ops& o0 = ops.t[0];
-    for (int e = threadIdx.x; e < C::DINV; e += blockDim.x) {
-      const int k1 = e % PO, k2 = (e / PO) % PO, k0 = e / (PO * PO);
-      dinv[e] = T(1) / (o0.lam[k0] + o0.lam[k1] + o0.lam[k2]);
-    }
-  }
   const int tid = threadIdx.x;
   const int lane = tid % TPP;
   const int pl = tid / TPP;
-  T* RA = reinterpret_cast<T*>(smem_raw + C::PREFIX) + (size_t)pl * C::PS;
+  T* RA = buf + (size_t)(pl < PPC ? pl : 0) * C::PS;
   T* RB = RA + C::RA;
 
-  const long long col = (long long)blockIdx.y * ndofs;
-  b += col;
-  x += col;
   const long long npatch = BND ? grid.n_bnd : grid.n_int;
-  const long long pidx = (long long)blockIdx.x * PPC + pl;
-  const bool valid = pidx < npatch;
+  const long long pidx = pbase + pl;
+  const bool valid = pl < PPC && pidx < npatch;
   int v[3], ty[3] = {0, 0, 0};
   if (BND) {
     int m[3] = {0, 0, 0};
@@ -191,15 +196,15 @@ __global__ void __launch_bounds__(I3<NN, T, BND>::THREADS, I3<NN, T, BND>::MINB)
         }
       }
       if (ld) {
-        i3_ldrun<NN, C::VW>(xb + off, &vin[q][0]);
-        i3_ldrun<NN, C::VW>(xb + off + ND, &vin[q][NN]);
+        i3_ldrun<NN, C::VW, T, NC>(xb + off, &vin[q][0]);
+        i3_ldrun<NN, C::VW, T, NC>(xb + off + ND, &vin[q][NN]);
       } else {
 #pragma unroll
         for (int c = 0; c < P; ++c) vin[q][c] = T(0);
       }
       // x halos of a main line: node n-1 of cell v0-2, node 0 of cell v0+1
-      hl[q][0] = (main && exlo[0]) ? __ldg(xb + off - ND + (NN - 1)) : T(0);
-      hl[q][1] = (main && exhi[0]) ? __ldg(xb + off + 2 * ND) : T(0);
+      hl[q][0] = (main && exlo[0]) ? ld_elem<NC>(xb + off - ND + (NN - 1)) : T(0);
+      hl[q][1] = (main && exhi[0]) ? ld_elem<NC>(xb + off + 2 * ND) : T(0);
     }
     i3_with_type<BND>(ty[0], [&](auto tc) {
       const Ops& ox = ops.t[decltype(tc)::value];
@@ -389,6 +394,20 @@ __global__ void __launch_bounds__(I3<NN, T, BND>::THREADS, I3<NN, T, BND>::MINB)
       }
     });
   }
+}
+
+template <int NN, typename T, bool BND>
+__global__ void __launch_bounds__(I3<NN, T, BND>::THREADS, I3<NN, T, BND>::MINB)
+    smooth_int3_kernel(const __grid_constant__ SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT> ops,
+                       int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
+                       PatchGrid grid) {
+  using C = I3<NN, T, BND>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* dinv = reinterpret_cast<T*>(smem_raw);
+  if constexpr (!BND) int3_dinv<NN, T>(ops.t[0], dinv);  // read after the first CTA barrier of the body
+  const long long col = (long long)blockIdx.y * ndofs;
+  int3_body<NN, T, BND, C::PPC, true>(ops, dinv, reinterpret_cast<T*>(smem_raw + C::PREFIX), (long long)blockIdx.x * C::PPC,
+                                colour, b + col, x + col, N, consistent, grid);
 }
 
 template <int NN, typename T, bool BND>

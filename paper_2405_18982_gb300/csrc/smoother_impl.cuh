@@ -756,37 +756,6 @@ cudaError_t launch_part(const sipg_handle* h, int level, int colour, const T* b,
 
 PatchGrid make_grid(int dim, int N, int colour);
 
-#include "smooth_int3.cuh"
-
-template <int DIM, int NN, bool BND, typename T>
-cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
-                           cudaStream_t s) {
-  if constexpr (DIM == 3 && sizeof(T) == 4)
-    if (use_int3<DIM, T>(g, b, x)) return launch_int3<NN, T, BND>(h, level, colour, b, x, g, s);
-  return launch_part<DIM, NN, BND, T>(h, level, colour, b, x, g, s);
-}
-
-template <typename T, int DIM, int NN>
-cudaError_t smooth_dispatch2(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s) {
-  const PatchGrid g = make_grid(DIM, h->lv[level].N, colour);
-  if (g.n_int + g.n_bnd <= 0) return cudaSuccess;  // no patch of this colour (N = 2)
-  cudaError_t e;
-  if (g.n_int > 0 && g.n_bnd > 0 && h->side) {
-    // the boundary-patch kernel runs beside the interior one (patches of one
-    // colour write disjoint nodes and read none that another one writes), so
-    // its CTAs fill the SMs the interior grid leaves idle in its last wave
-    if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    if ((e = launch_patches<DIM, NN, true, T>(h, level, colour, b, x, g, h->side)) != cudaSuccess) return e;
-    if ((e = launch_patches<DIM, NN, false, T>(h, level, colour, b, x, g, s)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
-    return cudaStreamWaitEvent(s, h->ev_join, 0);
-  }
-  e = launch_patches<DIM, NN, false, T>(h, level, colour, b, x, g, s);
-  if (e != cudaSuccess) return e;
-  return launch_patches<DIM, NN, true, T>(h, level, colour, b, x, g, s);
-}
-
 // ------------------------------------------------------------------ fused step
 // All 2^d colours of one smoothing step in one cooperative launch, for levels
 // whose colour passes are latency bound (one wave of CTAs).  Colours are
@@ -828,6 +797,38 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
   }
   __syncthreads();
   return ok != 0;
+}
+
+#include "smooth_int3.cuh"
+#include "smooth_w3.cuh"
+
+template <int DIM, int NN, bool BND, typename T>
+cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
+                           cudaStream_t s) {
+  if constexpr (DIM == 3 && sizeof(T) == 4)
+    if (use_int3<DIM, T>(g, b, x)) return launch_int3<NN, T, BND>(h, level, colour, b, x, g, s);
+  return launch_part<DIM, NN, BND, T>(h, level, colour, b, x, g, s);
+}
+
+template <typename T, int DIM, int NN>
+cudaError_t smooth_dispatch2(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s) {
+  const PatchGrid g = make_grid(DIM, h->lv[level].N, colour);
+  if (g.n_int + g.n_bnd <= 0) return cudaSuccess;  // no patch of this colour (N = 2)
+  cudaError_t e;
+  if (g.n_int > 0 && g.n_bnd > 0 && h->side) {
+    // the boundary-patch kernel runs beside the interior one (patches of one
+    // colour write disjoint nodes and read none that another one writes), so
+    // its CTAs fill the SMs the interior grid leaves idle in its last wave
+    if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_patches<DIM, NN, true, T>(h, level, colour, b, x, g, h->side)) != cudaSuccess) return e;
+    if ((e = launch_patches<DIM, NN, false, T>(h, level, colour, b, x, g, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, h->ev_join, 0);
+  }
+  e = launch_patches<DIM, NN, false, T>(h, level, colour, b, x, g, s);
+  if (e != cudaSuccess) return e;
+  return launch_patches<DIM, NN, true, T>(h, level, colour, b, x, g, s);
 }
 
 template <int DIM, int NN, typename T>
@@ -919,6 +920,15 @@ PatchGrid make_grid(int dim, int N, int colour) {
 // then launches the colours one by one).
 template <typename T, int DIM, int NN>
 cudaError_t step_dispatch2(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s) {
+  if constexpr (DIM == 3) {
+    // the smallest levels (at most 64 patches per colour): one patch per
+    // CTA, every stage spread over the CTA (latency, not throughput, bounds a
+    // colour pass there); measured on GB300, Q3: 60 / 59 us per FP32 step at
+    // N = 8 / 4 against 69 / 65 for the line kernels, 178 against 328 in FP64.
+    // At N = 16 (512 patches per colour) the line kernels stay ahead.
+    const int N = h->lv[level].N;
+    if (N <= 8) return stepw3_dispatch<NN, T>(h, level, reverse, b, x, s);
+  }
   using Cfg = StepCfg<DIM, NN, T>;
   if (Cfg::SMEM > 227 * 1024 || h->num_sms <= 0) return cudaErrorNotSupported;
   static int max_active = -1;

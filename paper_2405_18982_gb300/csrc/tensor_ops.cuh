@@ -81,14 +81,22 @@ template <> struct i3_vec<float, 1> { using t = float; };
 template <> struct i3_vec<double, 2> { using t = double2; };
 template <> struct i3_vec<double, 1> { using t = double; };
 
-// v[0..NN) = p[0..NN) through the read-only path (vector loads of width VW)
-template <int NN, int VW, typename T>
+// One element / vector through the read-only path (NC) or a plain,
+// coherent global load.
+template <bool NC, typename V>
+__device__ __forceinline__ V ld_elem(const V* p) {
+  if constexpr (NC) return __ldg(p);
+  else return *p;
+}
+
+// v[0..NN) = p[0..NN) by vector loads of width VW (read-only path if NC)
+template <int NN, int VW, typename T, bool NC = true>
 __device__ __forceinline__ void i3_ldrun(const T* __restrict__ p, T* v) {
   using V = typename i3_vec<T, VW>::t;
   const V* q = reinterpret_cast<const V*>(p);
 #pragma unroll
   for (int j = 0; j < NN / VW; ++j) {
-    const V w = __ldg(q + j);
+    const V w = ld_elem<NC>(q + j);
     const T* e = reinterpret_cast<const T*>(&w);
 #pragma unroll
     for (int c = 0; c < VW; ++c) v[j * VW + c] = e[c];

@@ -340,8 +340,9 @@ def test_single_level_is_direct():
 def test_fused_step_equals_colour_passes(case, prec):
     # one smoothing step launched as a single cooperative kernel (small
     # levels) gives the result of the colour-by-colour launches: bit-identical
-    # where both run the same patch kernel; 3D FP32 colour passes run the
-    # register-direct interior kernel (other summation order): FP32 rounding
+    # in 2D, where both run the same patch code; in 3D the fused step runs the
+    # wide patch kernel and the colour passes the line kernels (same dot
+    # products; the eigenvalue scaling rounds differently): rounding level
     import torch
     dim, k, l2, nl = case
     dt = torch.float64 if prec == SIPG_FP64 else torch.float32
@@ -356,7 +357,7 @@ def test_fused_step_equals_colour_passes(case, prec):
         order = range(2 ** dim)
         for c in (reversed(order) if reverse else order):
             s.smooth_colour(nl - 1, c, b, xb)
-        if dim == 3 and prec == SIPG_FP32:
-            assert rel_inf(host(xa), host(xb)) < 1e-5
+        if dim == 3:
+            assert rel_inf(host(xa), host(xb)) < (1e-5 if prec == SIPG_FP32 else 1e-13)
         else:
             assert torch.equal(xa, xb)
