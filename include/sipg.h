@@ -40,7 +40,8 @@
  *
  * Tuning (read by sipg_create): SIPG_FUSED_SMOOTHING=0 in the environment
  * turns off the single cooperative launch per smoothing step on small levels
- * (the colours are then launched one by one; the results are the same).
+ * (the colours are then launched one by one; the results are the same);
+ * SIPG_AUTOTUNE=0 skips the bind-time autotuning (sipg_tuning).
  */
 #ifndef SIPG_H
 #define SIPG_H
@@ -193,6 +194,16 @@ sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host
 /* out[r] = <a_r, b_r> for every column r (FP64, deterministic order),
  * written to device memory. */
 sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* out, void* stream);
+
+/* Autotuned launch choices of one level (no counterpart in the paper: a
+ * property of this implementation).  sipg_bind_workspace times, per level and
+ * for the V-cycle precision, every launch path of one smoothing step on the
+ * level's scratch vectors and keeps the fastest; this reports the choice.
+ * *path: -1 not tuned (default rules), 0 one fused launch per step, 1 colour
+ * by colour.  *tile: interior tile of the 3D FP32 colour pass, 0 the default
+ * patches per CTA, 1 half as many.  precision: SIPG_FP64 or SIPG_FP32.
+ * EINVAL for a bad level or precision or null outputs. */
+sipg_status sipg_tuning(const sipg_handle* h, int level, int precision, int* path, int* tile);
 
 /* ---- ragged batch: independent problems (any dim, degree, size) solved
  * together.  Each member is a full handle (its own levels, workspace slice,

@@ -208,6 +208,13 @@ class SIPG:
         return SolveInfo(info.iterations, info.status, info.rel_residual, info.nu,
                          [hist[i] for i in range(info.history_len)])
 
+    def tuning(self, level, precision=None):
+        """(path, tile) chosen by the bind-time autotuner for `level`."""
+        prec = self.params.vcycle_precision if precision is None else precision
+        path, tile = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.sipg_tuning(self.h, level, prec, ctypes.byref(path), ctypes.byref(tile)))
+        return path.value, tile.value
+
     def get_constants(self, level, which, ptype=0, cap=1 << 14, stream=None):
         import numpy as np
         buf = (ctypes.c_double * cap)()

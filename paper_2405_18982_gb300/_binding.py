@@ -75,6 +75,7 @@ SIGNATURES = {
     "sipg_dot_noalloc": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_selftest_barrier": (_st, [_vp, _i, _vp]),
     "sipg_get_constants": (_st, [_vp, _i, _i, _i, _vp, _i, ctypes.POINTER(_i), _vp]),
+    "sipg_tuning": (_st, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "sipg_batch_create": (_st, [ctypes.POINTER(sipg_params), _i, ctypes.POINTER(_vp)]),
     "sipg_batch_destroy": (None, [_vp]),
     "sipg_batch_last_error": (ctypes.c_char_p, [_vp]),

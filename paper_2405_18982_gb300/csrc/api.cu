@@ -370,6 +370,90 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
   return finish(runs[0]);
 }
 
+// Autotuning of the smoothing step, per level: time each candidate launch
+// path (colour by colour with the default or the half interior tile, or one
+// fused launch where that applies) on the level's workspace vectors (zeroed;
+// the arithmetic does not depend on the values) and keep the fastest.
+template <typename T>
+sipg_status tune_T(sipg_handle* h, cudaStream_t s) {
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  const int nl = h->L + 1;
+  h->tune_path[pi].assign(nl, -1);
+  h->tune_tile[pi].assign(nl, 0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SIPG_CHECK(cudaEventCreate(&e0), "event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(h, SIPG_ECUDA, "event");
+  }
+  sipg_status result = SIPG_OK;
+  for (int l = 1; l <= h->L && result == SIPG_OK; ++l) {
+    T* b = reinterpret_cast<T*>(h->vb(l));
+    T* x = reinterpret_cast<T*>(h->vx(l));
+    const size_t bytes = h->lv[l].ndofs * (size_t)h->prm.nrhs * sizeof(T);
+    if (cudaMemsetAsync(b, 0, bytes, s) != cudaSuccess || cudaMemsetAsync(x, 0, bytes, s) != cudaSuccess) {
+      result = fail(h, SIPG_ECUDA, "memset");
+      break;
+    }
+    struct Cand {
+      int path, tile;
+    };
+    std::vector<Cand> cands = {{1, 0}};
+    if (h->prm.dim == 3 && sizeof(T) == 4) cands.push_back({1, 1});
+    if (h->fuse_small_levels) cands.push_back({0, 0});
+    float best = 1e30f;
+    Cand pick = {-1, 0};
+    for (const Cand& c : cands) {
+      h->tune_path[pi][l] = c.path;
+      h->tune_tile[pi][l] = c.tile;
+      int launches = 0;
+      cudaError_t e = launch_smooth_step<T>(h, l, 0, b, x, s, &launches);  // warm-up
+      if (e != cudaSuccess) {
+        result = cuda_fail(h, e, "autotune");
+        break;
+      }
+      if (c.path == 0 && launches != 1) continue;  // no fused launch on this level
+      float ms = 0.f;
+      int reps = 1;
+      for (int round = 0; round < 2; ++round) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_smooth_step<T>(h, l, 0, b, x, s, &launches);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        // second round: enough repetitions for about 0.3 ms
+        reps = std::max(2, std::min(20, (int)(0.3f / std::max(ms / reps, 1e-4f))));
+      }
+      if (e != cudaSuccess) {
+        result = cuda_fail(h, e, "autotune");
+        break;
+      }
+      const float t = ms / reps;
+      if (t < best) {
+        best = t;
+        pick = c;
+      }
+    }
+    h->tune_path[pi][l] = pick.path;
+    h->tune_tile[pi][l] = pick.tile;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != SIPG_OK) return result;
+  // a fused launch whose bounded grid barrier gave up: keep colour-by-colour
+  int status = 0;
+  SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_sync + 2 * sizeof(unsigned int), sizeof(int),
+                             cudaMemcpyDeviceToHost, s),
+             "status D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  if (status != 0) {
+    SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+    for (int l = 1; l < nl; ++l) h->tune_path[pi][l] = 1;
+  }
+  return SIPG_OK;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -402,8 +486,10 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
 
   sipg_handle* h = new sipg_handle();
   h->prm = *p;
-  // tuning knob: SIPG_FUSED_SMOOTHING=0 launches small levels colour by colour
+  // tuning knobs: SIPG_FUSED_SMOOTHING=0 launches small levels colour by
+  // colour; SIPG_AUTOTUNE=0 skips the bind-time timing of the launch paths
   if (const char* env = getenv("SIPG_FUSED_SMOOTHING")) h->fuse_small_levels = atoi(env) != 0;
+  if (const char* env = getenv("SIPG_AUTOTUNE")) h->autotune = atoi(env) != 0;
   h->n = n;
   h->L = L;
   for (int l = 0; l <= L; ++l) {
@@ -531,6 +617,10 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
   SIPG_CHECK(cudaMemcpyAsync(h->hc32.data(), h->c32(0), sizeof(LevelConst<float>) * nl, cudaMemcpyDeviceToHost, s),
              "constants D2H");
   SIPG_CHECK(cudaStreamSynchronize(s), "setup sync");
+  if (h->autotune) {
+    const sipg_status st = h->prm.vcycle_precision == SIPG_FP32 ? tune_T<float>(h, s) : tune_T<double>(h, s);
+    if (st) return st;
+  }
   return SIPG_OK;
 }
 
@@ -787,6 +877,15 @@ sipg_status sipg_get_constants(sipg_handle* h, int level, int which, int type, d
   int cnt = std::min((int)v.size(), cap);
   for (int i = 0; i < cnt; ++i) host_out[i] = v[i];
   *count = (int)v.size();
+  return SIPG_OK;
+}
+
+sipg_status sipg_tuning(const sipg_handle* h, int level, int precision, int* path, int* tile) {
+  if (!h || !path || !tile) return SIPG_EINVAL;
+  if (level < 0 || level > h->L || (precision != SIPG_FP64 && precision != SIPG_FP32)) return SIPG_EINVAL;
+  const int pi = precision == SIPG_FP32 ? 1 : 0;
+  *path = h->tuned_path(pi, level);
+  *tile = h->tuned_tile(pi, level);
   return SIPG_OK;
 }
 

@@ -98,6 +98,18 @@ struct sipg_handle {
   int num_sms = 0;                           // of the device the workspace lives on
   KrylovScalars* pinned = nullptr;           // page-locked host copy of the scalars (nrhs)
   bool fuse_small_levels = true;             // one cooperative launch per smoothing step when it fits one wave
+  // autotuned choices per precision (0 FP64, 1 FP32) and level, measured at
+  // bind time unless SIPG_AUTOTUNE=0: smoothing-step path (-1 not tuned,
+  // 0 fused launch, 1 colour by colour) and interior tile of the 3D FP32
+  // colour pass (0 default patches per CTA, 1 half as many)
+  bool autotune = true;
+  std::vector<int> tune_path[2], tune_tile[2];
+  int tuned_path(int prec, int l) const {
+    return l >= 0 && l < (int)tune_path[prec].size() ? tune_path[prec][l] : -1;
+  }
+  int tuned_tile(int prec, int l) const {
+    return l >= 0 && l < (int)tune_tile[prec].size() ? tune_tile[prec][l] : 0;
+  }
   // second stream for the boundary-patch kernel of a colour pass, forked
   // from and joined to the calling stream with these events
   cudaStream_t side = nullptr;

@@ -28,7 +28,7 @@
 // memory, rows outside V_j with zero operators, S padded by the identity, the
 // residual zeroed outside V_j and halos outside the domain read as zero.
 
-template <int NN, typename T, bool BND>
+template <int NN, typename T, bool BND, int TILE = 0>
 struct I3 {
   static constexpr int P = 2 * NN;                      // patch nodes per direction
   static constexpr int PO = BND ? 2 * NN : 2 * NN - 2;  // rows per direction
@@ -50,9 +50,11 @@ struct I3 {
   static constexpr int PREFIX = (DINV * (int)sizeof(T) + 15) / 16 * 16;
   // patches per CTA: fill about 54 KB of shared memory (four CTAs per SM) with
   // at most 512 threads
+  // (TILE = 1: half as many, for the autotuner)
   static constexpr int ppc() {
     int k = (54 * 1024 - PREFIX) / (PS * (int)sizeof(T));
     if (k > 512 / TPP) k = 512 / TPP;
+    if (TILE == 1) k /= 2;
     return k < 1 ? 1 : k;
   }
   static constexpr int PPC = ppc();
@@ -64,7 +66,7 @@ struct I3 {
     int m = by_smem < by_thr ? by_smem : by_thr;
     // boundary patches: longer lines need more registers; they run beside
     // the interior kernel
-    const int cap = BND ? 2 : 4;
+    const int cap = BND ? 2 : (TILE == 1 ? 8 : 4);
     return m < 1 ? 1 : (m > cap ? cap : m);
   }
   static constexpr int MINB = minblocks();
@@ -396,12 +398,12 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
   }
 }
 
-template <int NN, typename T, bool BND>
-__global__ void __launch_bounds__(I3<NN, T, BND>::THREADS, I3<NN, T, BND>::MINB)
+template <int NN, typename T, bool BND, int TILE>
+__global__ void __launch_bounds__(I3<NN, T, BND, TILE>::THREADS, I3<NN, T, BND, TILE>::MINB)
     smooth_int3_kernel(const __grid_constant__ SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT> ops,
                        int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
                        PatchGrid grid) {
-  using C = I3<NN, T, BND>;
+  using C = I3<NN, T, BND, TILE>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* dinv = reinterpret_cast<T*>(smem_raw);
   if constexpr (!BND) int3_dinv<NN, T>(ops.t[0], dinv);  // read after the first CTA barrier of the body
@@ -410,15 +412,15 @@ __global__ void __launch_bounds__(I3<NN, T, BND>::THREADS, I3<NN, T, BND>::MINB)
                                 colour, b + col, x + col, N, consistent, grid);
 }
 
-template <int NN, typename T, bool BND>
+template <int NN, typename T, bool BND, int TILE>
 cudaError_t launch_int3(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
                         cudaStream_t s) {
-  using C = I3<NN, T, BND>;
+  using C = I3<NN, T, BND, TILE>;
   const long long np = BND ? g.n_bnd : g.n_int;
   if (np <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(smooth_int3_kernel<NN, T, BND>,
+    cudaError_t e = cudaFuncSetAttribute(smooth_int3_kernel<NN, T, BND, TILE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -426,7 +428,7 @@ cudaError_t launch_int3(const sipg_handle* h, int level, int colour, const T* b,
   SmoothOps<C::PO, C::P, T, C::NT> ops;
   for (int t = 0; t < C::NT; ++t) make_ops<C::PO, C::P, BND, T>(h->hcst<T>(level), t, ops.t[t]);
   dim3 grid((unsigned)((np + C::PPC - 1) / C::PPC), h->prm.nrhs);
-  smooth_int3_kernel<NN, T, BND><<<grid, C::THREADS, C::SMEM, s>>>(
+  smooth_int3_kernel<NN, T, BND, TILE><<<grid, C::THREADS, C::SMEM, s>>>(
       ops, colour, b, x, h->lv[level].N, h->prm.smoother == SIPG_SMOOTHER_CONSISTENT ? 1 : 0,
       (long long)h->lv[level].ndofs, g);
   return cudaGetLastError();

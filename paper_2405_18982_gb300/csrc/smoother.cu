@@ -52,7 +52,7 @@ template cudaError_t launch_smooth_colour<float>(const sipg_handle*, int, int, c
 template <typename T>
 cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s,
                                int* launches) {
-  if (h->fuse_small_levels) {
+  if (h->fuse_small_levels && h->tuned_path(sizeof(T) == 4 ? 1 : 0, level) != 1) {
     cudaError_t e = h->prm.dim == 2 ? step_dim<2, T>(h, level, reverse, b, x, s)
                                     : step_dim<3, T>(h, level, reverse, b, x, s);
     if (e == cudaSuccess) {

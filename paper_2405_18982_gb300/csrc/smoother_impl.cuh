@@ -805,8 +805,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
 template <int DIM, int NN, bool BND, typename T>
 cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
                            cudaStream_t s) {
-  if constexpr (DIM == 3 && sizeof(T) == 4)
-    if (use_int3<DIM, T>(g, b, x)) return launch_int3<NN, T, BND>(h, level, colour, b, x, g, s);
+  if constexpr (DIM == 3 && sizeof(T) == 4) {
+    if (use_int3<DIM, T>(g, b, x)) {
+      if (!BND && h->tuned_tile(1, level) == 1) return launch_int3<NN, T, BND, 1>(h, level, colour, b, x, g, s);
+      return launch_int3<NN, T, BND, 0>(h, level, colour, b, x, g, s);
+    }
+  }
   return launch_part<DIM, NN, BND, T>(h, level, colour, b, x, g, s);
 }
 

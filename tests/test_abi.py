@@ -92,3 +92,19 @@ def test_batch_host_only_calls_without_gpu(lib):
     assert lib.sipg_batch_solve(b, ptrs, xs, 1e-10, 10, None, None) == -8
     assert b"bound" in lib.sipg_batch_last_error(b)
     lib.sipg_batch_destroy(b)
+
+
+def test_tuning_query_without_gpu(lib):
+    from paper_2405_18982_gb300._binding import SIGNATURES, sipg_params
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    h = ctypes.c_void_p()
+    assert lib.sipg_create(ctypes.byref(sipg_params(3, 3, 4, 3, 1.0, 1.0, 1, 0, 1, 0)), ctypes.byref(h)) == 0
+    path, tile = ctypes.c_int(7), ctypes.c_int(7)
+    # not bound, so not tuned: default rules
+    assert lib.sipg_tuning(h, 2, 1, ctypes.byref(path), ctypes.byref(tile)) == 0
+    assert (path.value, tile.value) == (-1, 0)
+    assert lib.sipg_tuning(h, 3, 1, ctypes.byref(path), ctypes.byref(tile)) == -1  # no level 3
+    assert lib.sipg_tuning(h, 0, 5, ctypes.byref(path), ctypes.byref(tile)) == -1  # bad precision
+    lib.sipg_destroy(h)
