@@ -14,7 +14,7 @@ vectors.  With lambda = A^{-T} (u - u_obs) = A^{-1} (u - u_obs) (A symmetric):
 """
 import numpy as np
 
-from .assembly import assemble, mass_apply, penalty
+from .assembly import assemble, block_apply, element_blocks, mass_apply, penalty
 from .direct import GlobalFD
 
 
@@ -40,4 +40,18 @@ def loss_and_gradients(dim, k, N, f, kappa, gamma, u_obs):
     g_f = mass_apply(dim, k, N, lam)
     g_kappa = -(lam @ b) / kappa
     g_gamma = -kappa * (lam @ (Ap @ u))
+    return J, g_f, g_kappa, g_gamma, u, lam
+
+
+def loss_and_gradients_blocks(dim, k, N, f, kappa, gamma, u_obs):
+    """Same as ``loss_and_gradients`` with A_p u evaluated cell by cell from the
+    element blocks (no assembled matrix), for meshes too large to assemble."""
+    u, b, fd = forward(dim, k, N, f, kappa, gamma)
+    res = u - u_obs
+    J = 0.5 * res @ res
+    lam = fd.solve(res)
+    Apu = block_apply(dim, k, N, element_blocks(dim, k, N, 1.0, 1.0, part="penalty"), u).ravel()
+    g_f = mass_apply(dim, k, N, lam)
+    g_kappa = -(lam @ b) / kappa
+    g_gamma = -kappa * (lam @ Apu)
     return J, g_f, g_kappa, g_gamma, u, lam

@@ -83,3 +83,48 @@ def test_fp32_source_gets_fp32_gradient():
     assert u.dtype == torch.float64
     (0.5 * ((u - dev(u_obs).view(1, -1)) ** 2).sum()).backward()
     assert ft.grad.dtype == torch.float32 and torch.isfinite(ft.grad).all()
+
+
+def test_c5_fullsize_gradients():
+    # 3D Q3 on 32^3 cells (2.1M DoFs), 5 levels, mixed precision: u_obs from a
+    # solve with f_obs ~ N(0,1) (seed 5, kappa = 1); f ~ N(0,1) (seed 6) as an
+    # FP32 tensor, kappa ~ U[0.5, 2] (seed 7), gamma = 2k(k+1)/h.  Gradients
+    # against the oracle's exact ones and FP64 central differences (step 1e-6)
+    import torch
+    from oracle.adjoint import forward, loss_and_gradients_blocks
+    from paper_2405_18982_gb300.autograd import SolverCache, sipg_solve
+    dim, k, l2, nl = 3, 3, 5, 5
+    N = 1 << l2
+    nd = N ** dim * (k + 1) ** dim
+    gamma = penalty(k, N, 1.0)
+    u_obs = forward(dim, k, N, inputs.normal(5, nd), 1.0, gamma)[0]
+    f = inputs.normal(6, nd).astype(np.float32)
+    kappa = inputs.scalar_uniform(7, 0.5, 2.0)
+    cache = SolverCache(dim, k, l2, nl, vcycle_precision=SIPG_FP32)
+    uo = dev(u_obs).view(1, -1)
+    ft = dev(f, torch.float32).view(1, -1).requires_grad_(True)
+    kt = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    gt = torch.tensor(gamma, dtype=torch.float64, requires_grad=True)
+    u = sipg_solve(ft, kt, gt, cache, rtol=1e-11)
+    J = 0.5 * ((u - uo) ** 2).sum()
+    J.backward()
+    J_ref, gf_ref, gk_ref, gg_ref, _, _ = loss_and_gradients_blocks(dim, k, N, f.astype(np.float64), kappa, gamma,
+                                                                     u_obs)
+    print(f"C5: J={J.item():.6e} ref={J_ref:.6e} dJ/dkappa={kt.grad.item():.6e} ref={gk_ref:.6e} "
+          f"dJ/dgamma={gt.grad.item():.6e} ref={gg_ref:.6e}")
+    assert abs(J.item() - J_ref) < 1e-8 * abs(J_ref)
+    assert ft.grad.dtype == torch.float32
+    assert np.abs(host(ft.grad).ravel() - gf_ref).max() < 1e-5 * np.abs(gf_ref).max()
+    assert abs(kt.grad.item() - gk_ref) < 1e-7 * abs(gk_ref)
+    assert abs(gt.grad.item() - gg_ref) < 1e-6 * abs(gg_ref)
+
+    def Jval(kk, gg):
+        with torch.no_grad():
+            uu = sipg_solve(ft.detach(), kk, gg, cache, rtol=1e-11)
+            return 0.5 * ((uu - uo) ** 2).sum().item()
+
+    step = 1e-6
+    fd_k = (Jval(kappa * (1 + step), gamma) - Jval(kappa * (1 - step), gamma)) / (2 * kappa * step)
+    fd_g = (Jval(kappa, gamma * (1 + step)) - Jval(kappa, gamma * (1 - step))) / (2 * gamma * step)
+    assert abs(fd_k - kt.grad.item()) < 1e-4 * abs(kt.grad.item())
+    assert abs(fd_g - gt.grad.item()) < 1e-4 * abs(gt.grad.item())

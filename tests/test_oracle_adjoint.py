@@ -72,3 +72,16 @@ def test_gradients_match_central_differences(dim, k, N):
     dvec = rng.standard_normal(len(f))
     df = (Jof(f + step * dvec, kappa, gamma) - Jof(f - step * dvec, kappa, gamma)) / (2 * step)
     assert abs(df - gf @ dvec) < 1e-6 * abs(gf @ dvec)
+
+
+@pytest.mark.parametrize("dim,k,N", [(2, 3, 4), (3, 2, 4)])
+def test_block_gradients_equal_assembled_gradients(dim, k, N):
+    # the cell-by-cell evaluation of A_p u (for large meshes) gives the same
+    # gradients as the assembled penalty matrix
+    from oracle.adjoint import loss_and_gradients_blocks
+    f, u_obs = _setup(dim, k, N, 31)
+    kappa, gamma = 1.4, penalty(k, N, 1.0)
+    a = loss_and_gradients(dim, k, N, f, kappa, gamma, u_obs)
+    b = loss_and_gradients_blocks(dim, k, N, f, kappa, gamma, u_obs)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2]
+    assert abs(a[3] - b[3]) <= 1e-12 * abs(a[3])
