@@ -34,7 +34,7 @@ template <int NN, typename T>
 struct ApplyConst {
   T Ls[3][NN * NN];
   T alo[NN], glo[NN], ahi[NN], ghi[NN];
-  T M[NN * NN];
+  T Mw[NN], Ma[NN], Mu[NN];  // M = diag(Mw) + Mu Ma^T (GLL mass: diagonal plus rank one)
 };
 
 template <int DIM, int NN, typename T>
@@ -79,7 +79,29 @@ __device__ __forceinline__ void normal_line(const ApplyConst<NN, T>& C, const T*
   store_line<NN>(Zs + base, stride, o);
 }
 
-// dst (+)= M src along direction e for line l
+// dst (+)= M src along direction e for line l, with the mass as diagonal
+// plus rank one: 3n FMAs per line instead of n^2
+template <int DIM, int NN, typename T>
+__device__ __forceinline__ void mass_line_r1(const ApplyConst<NN, T>& C, const T* src, T* dst, int e, int l,
+                                             bool acc) {
+  using CS = CellShape<DIM, NN>;
+  int base, stride;
+  CS::line(e, l, base, stride);
+  T v[NN], o[NN];
+  load_line<NN>(src + base, stride, v);
+  T s = C.Ma[0] * v[0];
+#pragma unroll
+  for (int j = 1; j < NN; ++j) s = fma(C.Ma[j], v[j], s);
+#pragma unroll
+  for (int i = 0; i < NN; ++i) o[i] = fma(C.Mu[i], s, C.Mw[i] * v[i]);
+  if (acc) {
+#pragma unroll
+    for (int i = 0; i < NN; ++i) o[i] += dst[base + i * stride];
+  }
+  store_line<NN>(dst + base, stride, o);
+}
+
+// dst (+)= M src along direction e for line l (dense n x n mass)
 template <int DIM, int NN, typename T>
 __device__ __forceinline__ void mass_line(const T* M, const T* src, T* dst, int e, int l, bool acc) {
   using CS = CellShape<DIM, NN>;
@@ -111,8 +133,10 @@ __global__ void __launch_bounds__(CPB * CellShape<DIM, NN>::lines)
   if (bvec) bvec += col;
   const bool pen = (mode == APPLY_PENALTY);
   for (int t = 0; t < 3; ++t) copy_block<NN>(C.Ls[t], pen ? lc->Pself[t] : lc->Lself[t], tid, nth);
-  copy_block<NN>(C.M, lc->M, tid, nth);
   if (tid < NN) {
+    C.Mw[tid] = lc->Mw[tid];
+    C.Ma[tid] = lc->Ma[tid];
+    C.Mu[tid] = lc->Mu[tid];
     C.alo[tid] = pen ? lc->palo[tid] : lc->alo[tid];
     C.glo[tid] = pen ? lc->pglo[tid] : lc->glo[tid];
     C.ahi[tid] = pen ? lc->pahi[tid] : lc->ahi[tid];
@@ -141,22 +165,22 @@ __global__ void __launch_bounds__(CPB * CellShape<DIM, NN>::lines)
   T* out;  // shared buffer holding A x for the block's cells
   if (DIM == 2) {
     // y = M_y Z_0 + M_x Z_1
-    if (valid) mass_line<DIM, NN, T>(C.M, Z0 + off, X + off, 1, l, false);
+    if (valid) mass_line_r1<DIM, NN, T>(C, Z0 + off, X + off, 1, l, false);
     __syncthreads();
-    if (valid) mass_line<DIM, NN, T>(C.M, Z1 + off, X + off, 0, l, true);
+    if (valid) mass_line_r1<DIM, NN, T>(C, Z1 + off, X + off, 0, l, true);
     out = X;
   } else {
     if (valid) {
-      mass_line<DIM, NN, T>(C.M, Z0 + off, X + off, 1, l, false);
-      mass_line<DIM, NN, T>(C.M, Z2 + off, W + off, 0, l, false);
+      mass_line_r1<DIM, NN, T>(C, Z0 + off, X + off, 1, l, false);
+      mass_line_r1<DIM, NN, T>(C, Z2 + off, W + off, 0, l, false);
     }
     __syncthreads();
     if (valid) {
-      mass_line<DIM, NN, T>(C.M, Z1 + off, X + off, 0, l, true);
-      mass_line<DIM, NN, T>(C.M, W + off, Z0 + off, 1, l, false);
+      mass_line_r1<DIM, NN, T>(C, Z1 + off, X + off, 0, l, true);
+      mass_line_r1<DIM, NN, T>(C, W + off, Z0 + off, 1, l, false);
     }
     __syncthreads();
-    if (valid) mass_line<DIM, NN, T>(C.M, X + off, Z0 + off, 2, l, true);
+    if (valid) mass_line_r1<DIM, NN, T>(C, X + off, Z0 + off, 2, l, true);
     out = Z0;
   }
   __syncthreads();

@@ -26,9 +26,19 @@ template <int NN, typename T>
 struct A3Ops {
   T Ls[3][NN * NN];  // Lself of types 0 (interior), 1 (low face on boundary), 2 (high)
   T alo[NN], glo[NN], ahi[NN], ghi[NN];
-  T M[NN * NN];
+  T Mw[NN], Ma[NN], Mu[NN];  // mass = diag(Mw) + Mu Ma^T (GLL: diagonal plus rank one)
   T PcT[2][NN * NN];  // PcT[o][j * NN + i] = Pc[o][i][j]
 };
+
+// o = M v for the mass as diagonal plus rank one (3n FMAs instead of n^2)
+template <int NN, typename T>
+__device__ __forceinline__ void a3_mass(const A3Ops<NN, T>& op, const T (&v)[NN], T (&o)[NN]) {
+  T s = op.Ma[0] * v[0];
+#pragma unroll
+  for (int j = 1; j < NN; ++j) s = fma(op.Ma[j], v[j], s);
+#pragma unroll
+  for (int i = 0; i < NN; ++i) o[i] = fma(op.Mu[i], s, op.Mw[i] * v[i]);
+}
 
 template <int NN, typename T>
 struct A3 {
@@ -172,12 +182,12 @@ __global__ void __launch_bounds__(A3<NN, T>::THREADS)
     T v[NN], u[NN];
 #pragma unroll
     for (int j = 0; j < NN; ++j) v[j] = Z1[q * CSZ + base + j];
-    matvec_line<NN>(op.M, v, u);
+    a3_mass<NN, T>(op, v, u);
 #pragma unroll
     for (int j = 0; j < NN; ++j) Xq[base + j] = u[j];
 #pragma unroll
     for (int j = 0; j < NN; ++j) v[j] = Z2[q * CSZ + base + j];
-    matvec_line<NN>(op.M, v, u);
+    a3_mass<NN, T>(op, v, u);
 #pragma unroll
     for (int j = 0; j < NN; ++j) Z2[q * CSZ + base + j] = u[j];
   }
@@ -189,12 +199,12 @@ __global__ void __launch_bounds__(A3<NN, T>::THREADS)
     T v[NN], t[NN];
 #pragma unroll
     for (int j = 0; j < NN; ++j) v[j] = Z0[q * CSZ + base + j * st];
-    matvec_line<NN>(op.M, v, t);
+    a3_mass<NN, T>(op, v, t);
 #pragma unroll
     for (int j = 0; j < NN; ++j) Z0[q * CSZ + base + j * st] = t[j] + Xq[base + j * st];
 #pragma unroll
     for (int j = 0; j < NN; ++j) v[j] = Z2[q * CSZ + base + j * st];
-    matvec_line<NN>(op.M, v, t);
+    a3_mass<NN, T>(op, v, t);
 #pragma unroll
     for (int j = 0; j < NN; ++j) Z1[q * CSZ + base + j * st] = t[j];
   }
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(A3<NN, T>::THREADS)
     T v[NN], r[NN];
 #pragma unroll
     for (int j = 0; j < NN; ++j) v[j] = Z0[q * CSZ + base + j * st];
-    matvec_line<NN>(op.M, v, r);
+    a3_mass<NN, T>(op, v, r);
 #pragma unroll
     for (int j = 0; j < NN; ++j) r[j] += Z1[q * CSZ + base + j * st];
     const long long gb = cell * ND + l0 + NN * l1;
@@ -317,8 +327,10 @@ A3Ops<NN, T> a3_ops(const LevelConst<T>& lc) {
     op.glo[i] = lc.glo[i];
     op.ahi[i] = lc.ahi[i];
     op.ghi[i] = lc.ghi[i];
+    op.Mw[i] = lc.Mw[i];
+    op.Ma[i] = lc.Ma[i];
+    op.Mu[i] = lc.Mu[i];
     for (int j = 0; j < NN; ++j) {
-      op.M[i * NN + j] = lc.M[i][j];
       op.PcT[0][i * NN + j] = lc.Pc[0][j][i];
       op.PcT[1][i * NN + j] = lc.Pc[1][j][i];
     }

@@ -178,6 +178,7 @@ __device__ bool generalised_eigen(int m, const double* A, const double* B, int l
 
 struct Basis1D {
   double xi[SIPG_MAXN];
+  double lead[SIPG_MAXN];          // leading coefficient of phi_j: 1 / prod_{m != j} (xi_j - xi_m)
   double D[SIPG_MAXN][SIPG_MAXN];  // D[i][j] = phi_j'(xi_i) (reference)
   double Mhat[SIPG_MAXN][SIPG_MAXN];
   double Khat[SIPG_MAXN][SIPG_MAXN];
@@ -194,6 +195,7 @@ __device__ void build_basis(int k, Basis1D& B) {
     for (int m = 0; m < n; ++m)
       if (m != j) p *= (B.xi[j] - B.xi[m]);
     bw[j] = 1.0 / p;
+    B.lead[j] = bw[j];
   }
   for (int i = 0; i < n; ++i) {
     double diag = 0.0;
@@ -306,6 +308,14 @@ __global__ void setup_levels_kernel(LevelConst<double>* out, int k, int N_finest
         c.Pc[0][i][j] = B.Pc[0][i][j];
         c.Pc[1][i][j] = B.Pc[1][i][j];
       }
+    }
+    // rank-one part e a a^T of Mhat from its first and last nodes' coupling
+    // (the largest |a_0 a_k|), then the diagonal remainder (the GLL weights)
+    const double e = B.Mhat[0][n - 1] / (B.lead[0] * B.lead[n - 1]);
+    for (int i = 0; i < n; ++i) {
+      c.Ma[i] = B.lead[i];
+      c.Mu[i] = h * e * B.lead[i];
+      c.Mw[i] = h * (B.Mhat[i][i] - e * B.lead[i] * B.lead[i]);
     }
   }
   __syncthreads();
@@ -421,6 +431,9 @@ __global__ void constants_to_float_kernel(const LevelConst<double>* in, LevelCon
     const int cnt = sizeof(a.field) / sizeof(double);                              \
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = (float)src[i];    \
   }
+  SIPG_CONVERT(Mw)
+  SIPG_CONVERT(Ma)
+  SIPG_CONVERT(Mu)
   SIPG_CONVERT(Lself)
   SIPG_CONVERT(alo)
   SIPG_CONVERT(glo)

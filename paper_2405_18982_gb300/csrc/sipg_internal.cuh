@@ -35,6 +35,11 @@ struct LevelConst {
   T Pself[3][SIPG_MAXN][SIPG_MAXN];
   T palo[SIPG_MAXN], pglo[SIPG_MAXN], pahi[SIPG_MAXN], pghi[SIPG_MAXN];
   T M[SIPG_MAXN][SIPG_MAXN];  // 1D cell mass h * Mhat
+  // The exact mass on Gauss-Lobatto nodes is diagonal plus rank one: the
+  // (2n-3)-exact GLL rule integrates phi_i phi_j up to a multiple of the
+  // product of the leading coefficients a_i a_j, so
+  //   M = diag(Mw) + Mu Ma^T   (Mw = h w_gll, Ma = a, Mu = h e a).
+  T Mw[SIPG_MAXN], Ma[SIPG_MAXN], Mu[SIPG_MAXN];
   // Vertex-patch 1D data per type t (bit 0: low end on the domain boundary,
   // bit 1: high end).  Patch-local 1D node a = o*n + i, o in {0,1}.  V_j keeps
   // a in [first, first+p).  Lr/Mr are the rows V_j of the 1D patch matrices

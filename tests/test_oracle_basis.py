@@ -68,3 +68,19 @@ def test_lagrange_interpolation_properties(k):
         assert np.allclose(Vt @ nodes ** p, t ** p, atol=1e-12)
         dp = p * t ** (p - 1) if p > 0 else np.zeros_like(t)
         assert np.allclose(Dt @ nodes ** p, dp, atol=1e-10)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7])
+def test_exact_gll_mass_is_diagonal_plus_rank_one(k):
+    # the n-point GLL rule is exact up to degree 2n-3, phi_i phi_j has degree
+    # 2n-2, so M_ij - w_i delta_ij = E(x^(2k)) lead(phi_i) lead(phi_j): the
+    # exact mass minus the GLL weights is a rank-one matrix built from the
+    # leading coefficients 1 / prod_{m != i} (xi_i - xi_m)
+    from oracle.assembly import mass_matrix_cell
+    xi, w = gauss_lobatto(k)
+    M = mass_matrix_cell(1, k, 1)
+    lead = np.array([1.0 / np.prod([xi[i] - xi[m] for m in range(k + 1) if m != i]) for i in range(k + 1)])
+    R = M - np.diag(w)
+    e = R[0, k] / (lead[0] * lead[k])
+    assert np.abs(R - e * np.outer(lead, lead)).max() < 1e-13 * np.abs(M).max()
+    assert np.linalg.matrix_rank(R, tol=1e-10 * np.abs(R).max()) == 1
