@@ -219,7 +219,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
                                   : (2 * P + (t - P * P) / P) * SA1 + PO * ((t - P * P) % P);
         T oa[PO];
         T(&vq)[P] = vin[q];
-        mass_rows<PO, P, NN, OFF>(ox.Mm, vq, oa);
+        mass_rows1<PO, P, NN, OFF>(ox, vq, oa);
         i3_st_pairs<PO>(RA + dst, oa);
         if (t < P * P) {
           T ob[PO];
@@ -256,9 +256,9 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
             vb[a1] = RA[P * SA1 + SA1 * a1 + t];
           }
           const T h0 = RA[2 * P * SA1 + t], h1 = RA[(2 * P + 1) * SA1 + t];
-          mass_rows<PO, P, NN, OFF>(oy.Mm, va, oc);
+          mass_rows1<PO, P, NN, OFF>(oy, va, oc);
           sipg_rows<PO, P, NN, OFF>(oy, va, h0, h1, od);
-          mass_rows_acc<PO, P, NN, OFF>(oy.Mm, vb, od);
+          mass_rows1_acc<PO, P, NN, OFF>(oy, vb, od);
 #pragma unroll
           for (int r1 = 0; r1 < PO; ++r1) {
             Cc[SC * a2 + PO * r1 + r0] = oc[r1];
@@ -269,7 +269,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
           T vz[P], oc[PO];
 #pragma unroll
           for (int a1 = 0; a1 < P; ++a1) vz[a1] = RA[(2 * P + 2 + side) * SA1 + PO * a1 + r0];
-          mass_rows<PO, P, NN, OFF>(oy.Mm, vz, oc);
+          mass_rows1<PO, P, NN, OFF>(oy, vz, oc);
 #pragma unroll
           for (int r1 = 0; r1 < PO; ++r1) CZ[side * CZS + PO * r1 + r0] = oc[r1];
         }
@@ -310,7 +310,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
         vd[a2] = Dd[SC * a2 + lane];
       }
       sipg_rows<PO, P, NN, OFF>(oz, vc, CZ[lane], CZ[CZS + lane], o);
-      mass_rows_acc<PO, P, NN, OFF>(oz.Mm, vd, o);
+      mass_rows1_acc<PO, P, NN, OFF>(oz, vd, o);
 #pragma unroll
       for (int r2 = 0; r2 < PO; ++r2) {
         const bool in = inxy && r2 >= zlo && r2 <= zhi;

@@ -37,28 +37,30 @@ struct W3 {
   static constexpr int R1 = i3_max(P * P * P + 6 * P * P, PO * PO * PO);
   static constexpr int R2 = i3_max(2 * P * P * PO + 4 * P * PO, PO * PO * PO);
   static constexpr int R3 = i3_max(2 * P * PO * PO + 2 * PO * PO, PO * PO * PO);
-  // operator sets: Lm, Mm (PO x LP), hlo, hhi, lam (PO), S (PO x SP), first, last
-  static constexpr int OPS = 2 * PO * LP + 3 * PO + PO * SP + 2;
+  // operator sets: Lm (PO x LP), mw, mu (PO), ma (n), hlo, hhi, lam (PO),
+  // S (PO x SP), first, last; the mass rows are diagonal plus rank one per cell
+  static constexpr int OPS = PO * LP + 2 * PO + NN + 3 * PO + PO * SP + 2;
   static constexpr size_t SMEM = sizeof(T) * ((size_t)NT * OPS + R1 + R2 + R3);
 };
 
 // copy the operator sets of the kernel parameters into padded rows
 template <int PO, int P, typename T, int NT>
 __device__ __forceinline__ void w3_ops_setup(const SmoothOps<PO, P, T, NT>& ops, T* dst) {
-  constexpr int LP = P + 1, SP = PO + 1, OPS = 2 * PO * LP + 3 * PO + PO * SP + 2;
+  constexpr int NN = P / 2, LP = P + 1, SP = PO + 1, OPS = PO * LP + 2 * PO + NN + 3 * PO + PO * SP + 2;
+  constexpr int MW = PO * LP, MU = MW + PO, MA = MU + PO, HL = MA + NN, HH = HL + PO, LA = HH + PO, SS = LA + PO;
   for (int t = 0; t < NT; ++t) {
     const Ops1D<PO, P, T>& o = ops.t[t];
     T* d = dst + t * OPS;
-    for (int e = threadIdx.x; e < PO * P; e += blockDim.x) {
-      d[(e / P) * LP + e % P] = o.Lm[e];
-      d[PO * LP + (e / P) * LP + e % P] = o.Mm[e];
-    }
+    for (int e = threadIdx.x; e < PO * P; e += blockDim.x) d[(e / P) * LP + e % P] = o.Lm[e];
     for (int e = threadIdx.x; e < PO; e += blockDim.x) {
-      d[2 * PO * LP + e] = o.hlo[e];
-      d[2 * PO * LP + PO + e] = o.hhi[e];
-      d[2 * PO * LP + 2 * PO + e] = o.lam[e];
+      d[MW + e] = o.mw[e];
+      d[MU + e] = o.mu[e];
+      d[HL + e] = o.hlo[e];
+      d[HH + e] = o.hhi[e];
+      d[LA + e] = o.lam[e];
     }
-    for (int e = threadIdx.x; e < PO * PO; e += blockDim.x) d[2 * PO * LP + 3 * PO + (e / PO) * SP + e % PO] = o.S[e];
+    for (int e = threadIdx.x; e < NN; e += blockDim.x) d[MA + e] = o.ma[e];
+    for (int e = threadIdx.x; e < PO * PO; e += blockDim.x) d[SS + (e / PO) * SP + e % PO] = o.S[e];
     if (threadIdx.x == 0) {
       d[OPS - 2] = T(o.first);
       d[OPS - 1] = T(o.last);
@@ -72,12 +74,26 @@ template <int NN, typename T, bool BND>
 struct W3View {
   using C = W3<NN, T, BND>;
   const T* base;
+  static constexpr int MW = C::PO * C::LP, MU = MW + C::PO, MA = MU + C::PO, HL = MA + NN, HH = HL + C::PO,
+                       LA = HH + C::PO, SS = LA + C::PO;
   __device__ const T* Lm() const { return base; }
-  __device__ const T* Mm() const { return base + C::PO * C::LP; }
-  __device__ const T* hlo() const { return base + 2 * C::PO * C::LP; }
-  __device__ const T* hhi() const { return base + 2 * C::PO * C::LP + C::PO; }
-  __device__ const T* lam() const { return base + 2 * C::PO * C::LP + 2 * C::PO; }
-  __device__ const T* S() const { return base + 2 * C::PO * C::LP + 3 * C::PO; }
+  __device__ const T* mw() const { return base + MW; }
+  __device__ const T* mu() const { return base + MU; }
+  __device__ const T* ma() const { return base + MA; }
+  __device__ const T* hlo() const { return base + HL; }
+  __device__ const T* hhi() const { return base + HH; }
+  __device__ const T* lam() const { return base + LA; }
+  __device__ const T* S() const { return base + SS; }
+  // acc + (mass row r) . in: diagonal plus rank one over the cell of row r,
+  // in(c) = element c of the input line
+  template <int OFF, class F>
+  __device__ T mass(int r, F in, T acc) const {
+    const int c0 = ((r + OFF) / NN) * NN;
+    T d = ma()[0] * in(c0);
+#pragma unroll
+    for (int j = 1; j < NN; ++j) d = fma(ma()[j], in(c0 + j), d);
+    return fma(mu()[r], d, fma(mw()[r], in(r + OFF), acc));
+  }
   __device__ int first() const { return (int)base[C::OPS - 2]; }
   __device__ int last() const { return (int)base[C::OPS - 1]; }
 };
@@ -186,11 +202,7 @@ __device__ __forceinline__ void w3_patch(const T* sops, T* buf, long long pidx, 
     if (e < P2 * PO) {  // A
       const int r0 = e % PO, line = e / PO;
       const T* in = X + line * P;
-      const int c0 = ((r0 + OFF) / NN) * NN;
-      T s = T(0);
-#pragma unroll
-      for (int c = 0; c < NN; ++c) s = fma(ox.Mm()[r0 * LP + c0 + c], in[c0 + c], s);
-      A[e] = s;
+      A[e] = ox.template mass<OFF>(r0, [&](int c) { return in[c]; }, T(0));
     } else if (e < 2 * P2 * PO) {  // B
       const int f = e - P2 * PO, r0 = f % PO, line = f / PO;
       const T* in = X + line * P;
@@ -201,11 +213,7 @@ __device__ __forceinline__ void w3_patch(const T* sops, T* buf, long long pidx, 
     } else {  // M_x on the y faces (lines (s, a2)) and z faces (lines (s, a1))
       const int f = e - 2 * P2 * PO, r0 = f % PO, line = f / PO;  // line in [0, 4P)
       const T* in = (line < 2 * P ? HY : HZ) + (line % (2 * P)) * P;
-      const int c0 = ((r0 + OFF) / NN) * NN;
-      T s = T(0);
-#pragma unroll
-      for (int c = 0; c < NN; ++c) s = fma(ox.Mm()[r0 * LP + c0 + c], in[c0 + c], s);
-      AHy[f] = s;  // AHy and AHz are contiguous
+      AHy[f] = ox.template mass<OFF>(r0, [&](int c) { return in[c]; }, T(0));  // AHy and AHz are contiguous
     }
   }
   __syncthreads();
@@ -220,30 +228,20 @@ __device__ __forceinline__ void w3_patch(const T* sops, T* buf, long long pidx, 
       const bool isD = e >= P * PO2;
       const int f = isD ? e - P * PO2 : e;
       const int r0 = f % PO, r1 = (f / PO) % PO, a2 = f / PO2;
-      const int c0 = ((r1 + OFF) / NN) * NN;
       const T* a = A + a2 * P * PO + r0;  // A[a2][c][r0] at a[c * PO]
       if (!isD) {
-        T s = T(0);
-#pragma unroll
-        for (int c = 0; c < NN; ++c) s = fma(oy.Mm()[r1 * LP + c0 + c], a[(c0 + c) * PO], s);
-        Cc[f] = s;
+        Cc[f] = oy.template mass<OFF>(r1, [&](int c) { return a[c * PO]; }, T(0));
       } else {
         const T* bm = B + a2 * P * PO + r0;
         T s = oy.hlo()[r1] * AHy[a2 * PO + r0] + oy.hhi()[r1] * AHy[P * PO + a2 * PO + r0];
 #pragma unroll
         for (int c = 0; c < P; ++c) s = fma(oy.Lm()[r1 * LP + c], a[c * PO], s);
-#pragma unroll
-        for (int c = 0; c < NN; ++c) s = fma(oy.Mm()[r1 * LP + c0 + c], bm[(c0 + c) * PO], s);
-        Dd[f] = s;
+        Dd[f] = oy.template mass<OFF>(r1, [&](int c) { return bm[c * PO]; }, s);
       }
     } else {
       const int f = e - 2 * P * PO2, r0 = f % PO, r1 = (f / PO) % PO, s = f / PO2;
-      const int c0 = ((r1 + OFF) / NN) * NN;
       const T* a = AHz + s * P * PO + r0;
-      T acc = T(0);
-#pragma unroll
-      for (int c = 0; c < NN; ++c) acc = fma(oy.Mm()[r1 * LP + c0 + c], a[(c0 + c) * PO], acc);
-      CZ[f] = acc;
+      CZ[f] = oy.template mass<OFF>(r1, [&](int c) { return a[c * PO]; }, T(0));
     }
   }
   __syncthreads();
@@ -255,13 +253,11 @@ __device__ __forceinline__ void w3_patch(const T* sops, T* buf, long long pidx, 
     const int e = tid + k * TPP;
     if (e < PO3) {
       const int r0 = e % PO, r1 = (e / PO) % PO, r2 = e / PO2;
-      const int c0 = ((r2 + OFF) / NN) * NN;
       const int col = r1 * PO + r0;
       T s = oz.hlo()[r2] * CZ[col] + oz.hhi()[r2] * CZ[PO2 + col];
 #pragma unroll
       for (int c = 0; c < P; ++c) s = fma(oz.Lm()[r2 * LP + c], Cc[c * PO2 + col], s);
-#pragma unroll
-      for (int c = 0; c < NN; ++c) s = fma(oz.Mm()[r2 * LP + c0 + c], Dd[(c0 + c) * PO2 + col], s);
+      s = oz.template mass<OFF>(r2, [&](int c) { return Dd[c * PO2 + col]; }, s);
       Rr[e] = inside(r0, r1, r2) ? bv[k] - s : T(0);
     }
   }

@@ -74,7 +74,9 @@ struct SC {
 template <int PO, int P, typename T>
 struct Ops1D {
   T Lm[PO * P];   // SIPG rows (patch columns only)
-  T Mm[PO * P];   // mass rows
+  // mass rows, block diagonal by cell and, with the GLL mass, diagonal plus
+  // rank one per cell: row r (patch node a) = mw[r] e_a + mu[r] (ma on a's cell)
+  T mw[PO], mu[PO], ma[P / 2];
   T hlo[PO], hhi[PO];
   T S[PO * PO];   // S[j][i]: row j, column i (column i = eigenvector i)
   T lam[PO];
@@ -91,30 +93,36 @@ constexpr int smooth_prefix_bytes() {
   return (bytes + 15) / 16 * 16;
 }
 
-// out[r] = sum over the cell of row r of Mm[r][c] v[c] (block-diagonal rows)
+// Same rows with the mass as diagonal plus rank one per cell: one dot
+// product per patch cell, then two FMAs per row
 template <int PO, int P, int NN, int OFF, typename T>
-__device__ __forceinline__ void mass_rows(const T* __restrict__ Mm, const T (&v)[P], T (&o)[PO]) {
+__device__ __forceinline__ void mass_rows1(const Ops1D<PO, P, T>& op, const T (&v)[P], T (&o)[PO]) {
+  T s[2];
 #pragma unroll
-  for (int r = 0; r < PO; ++r) {
-    const int c0 = ((r + OFF) / NN) * NN;
-    T s = Mm[r * P + c0] * v[c0];
+  for (int c = 0; c < 2; ++c) {
+    T a = op.ma[0] * v[c * NN];
 #pragma unroll
-    for (int c = 1; c < NN; ++c) s = fma(Mm[r * P + c0 + c], v[c0 + c], s);
-    o[r] = s;
+    for (int j = 1; j < NN; ++j) a = fma(op.ma[j], v[c * NN + j], a);
+    s[c] = a;
   }
+#pragma unroll
+  for (int r = 0; r < PO; ++r) o[r] = fma(op.mu[r], s[(r + OFF) / NN], op.mw[r] * v[r + OFF]);
 }
 
 template <int PO, int P, int NN, int OFF, typename T>
-__device__ __forceinline__ void mass_rows_acc(const T* __restrict__ Mm, const T (&v)[P], T (&o)[PO]) {
+__device__ __forceinline__ void mass_rows1_acc(const Ops1D<PO, P, T>& op, const T (&v)[P], T (&o)[PO]) {
+  T s[2];
 #pragma unroll
-  for (int r = 0; r < PO; ++r) {
-    const int c0 = ((r + OFF) / NN) * NN;
-    T s = o[r];
+  for (int c = 0; c < 2; ++c) {
+    T a = op.ma[0] * v[c * NN];
 #pragma unroll
-    for (int c = 0; c < NN; ++c) s = fma(Mm[r * P + c0 + c], v[c0 + c], s);
-    o[r] = s;
+    for (int j = 1; j < NN; ++j) a = fma(op.ma[j], v[c * NN + j], a);
+    s[c] = a;
   }
+#pragma unroll
+  for (int r = 0; r < PO; ++r) o[r] = fma(op.mu[r], s[(r + OFF) / NN], fma(op.mw[r], v[r + OFF], o[r]));
 }
+
 
 // Structural nonzeros of the 1D patch SIPG matrix (rows/columns = patch
 // nodes a, c): the own cell is dense; the coupling to the other patch cell is
@@ -217,12 +225,15 @@ void make_ops(const LevelConst<T>& lc, int t, Ops1D<PO, P, T>& op) {
     const bool in = BND ? (rv >= 0 && rv < p) : true;
     for (int c = 0; c < P; ++c) {
       op.Lm[r * P + c] = in ? lc.Lr[t][rv][1 + c] : T(0);
-      op.Mm[r * P + c] = in ? lc.Mr[t][rv][1 + c] : T(0);
     }
     op.hlo[r] = in ? lc.Lr[t][rv][0] : T(0);
     op.hhi[r] = in ? lc.Lr[t][rv][P + 1] : T(0);
     op.lam[r] = in ? lc.lam[t][rv] : T(1);
+    const int node = (r + (BND ? 0 : 1)) % (P / 2);  // local node of row r in its cell
+    op.mw[r] = in ? lc.Mw[node] : T(0);
+    op.mu[r] = in ? lc.Mu[node] : T(0);
   }
+  for (int j = 0; j < P / 2; ++j) op.ma[j] = lc.Ma[j];
   for (int j = 0; j < PO; ++j)
     for (int i = 0; i < PO; ++i) {
       const int jv = j - off, iv = i - off;
@@ -469,7 +480,7 @@ __device__ __forceinline__ void smooth_chunk(
           const int a1 = t % P, a2 = t / P;
           T vin[P], oa[PO], ob[PO];
           ld<P>(X + (a2 * P + a1) * SX, 1, vin);
-          mass_rows<PO, P, NN, OFF>(ox.Mm, vin, oa);
+          mass_rows1<PO, P, NN, OFF>(ox, vin, oa);
           sipg_rows<PO, P, NN, OFF>(ox, vin, Hx[a2 * P + a1], Hx[P * P + a2 * P + a1], ob);
           st<PO>(A + (a2 * P + a1) * SO, 1, oa);
           st<PO>(Bm + (a2 * P + a1) * SO, 1, ob);
@@ -477,7 +488,7 @@ __device__ __forceinline__ void smooth_chunk(
           const int h = t - P * P;  // slot * P + line
           T vin[P], oa[PO];
           ld<P>(Hyz + h * SX, 1, vin);
-          mass_rows<PO, P, NN, OFF>(ox.Mm, vin, oa);
+          mass_rows1<PO, P, NN, OFF>(ox, vin, oa);
           st<PO>(AH + h * SO, 1, oa);
         }
       });
@@ -494,17 +505,17 @@ __device__ __forceinline__ void smooth_chunk(
           T va[P], vb[P], oc[PO], od[PO];
           ld<P>(A + a2 * P * SO + r0, SO, va);
           ld<P>(Bm + a2 * P * SO + r0, SO, vb);
-          mass_rows<PO, P, NN, OFF>(oy.Mm, va, oc);
+          mass_rows1<PO, P, NN, OFF>(oy, va, oc);
           // y-halo faces with M_x applied: AH slots 0 (lo), 1 (hi), line a2
           sipg_rows<PO, P, NN, OFF>(oy, va, AH[(0 * P + a2) * SO + r0], AH[(1 * P + a2) * SO + r0], od);
-          mass_rows_acc<PO, P, NN, OFF>(oy.Mm, vb, od);
+          mass_rows1_acc<PO, P, NN, OFF>(oy, vb, od);
           st<PO>(Cc + a2 * PO * PO + r0, PO, oc);
           st<PO>(Dd + a2 * PO * PO + r0, PO, od);
         } else {
           const int q = t - PO * P, side = q / PO, r0 = q % PO;
           T va[P], oc[PO];
           ld<P>(AH + (2 + side) * P * SO + r0, SO, va);  // z faces, lines indexed by a1
-          mass_rows<PO, P, NN, OFF>(oy.Mm, va, oc);
+          mass_rows1<PO, P, NN, OFF>(oy, va, oc);
           st<PO>(Cz + side * PO * PO + r0, PO, oc);
         }
       });
@@ -519,7 +530,7 @@ __device__ __forceinline__ void smooth_chunk(
         ld<P>(Cc + r1 * PO + r0, PO * PO, vc);
         ld<P>(Dd + r1 * PO + r0, PO * PO, vd);
         sipg_rows<PO, P, NN, OFF>(oz, vc, Cz[r1 * PO + r0], Cz[PO * PO + r1 * PO + r0], o);
-        mass_rows_acc<PO, P, NN, OFF>(oz.Mm, vd, o);
+        mass_rows1_acc<PO, P, NN, OFF>(oz, vd, o);
         const bool inxy = !BND || (r0 >= ox.first && r0 <= ox.last && r1 >= oy.first && r1 <= oy.last);
 #pragma unroll
         for (int r2 = 0; r2 < PO; ++r2) {
@@ -610,7 +621,7 @@ __device__ __forceinline__ void smooth_chunk(
         if (t < P) {
           T vin[P], oa[PO], ob[PO];
           ld<P>(X + t * SX, 1, vin);
-          mass_rows<PO, P, NN, OFF>(ox.Mm, vin, oa);
+          mass_rows1<PO, P, NN, OFF>(ox, vin, oa);
           sipg_rows<PO, P, NN, OFF>(ox, vin, Hx[t], Hx[P + t], ob);
           st<PO>(A + t * SO, 1, oa);
           st<PO>(Bm + t * SO, 1, ob);
@@ -618,7 +629,7 @@ __device__ __forceinline__ void smooth_chunk(
           const int side = t - P;
           T vin[P], oa[PO];
           ld<P>(Hyz + side * SX, 1, vin);
-          mass_rows<PO, P, NN, OFF>(ox.Mm, vin, oa);
+          mass_rows1<PO, P, NN, OFF>(ox, vin, oa);
           st<PO>(AH + side * SO, 1, oa);
         }
       });
@@ -632,7 +643,7 @@ __device__ __forceinline__ void smooth_chunk(
         ld<P>(A + r0, SO, va);
         ld<P>(Bm + r0, SO, vb);
         sipg_rows<PO, P, NN, OFF>(oy, va, AH[r0], AH[SO + r0], o);
-        mass_rows_acc<PO, P, NN, OFF>(oy.Mm, vb, o);
+        mass_rows1_acc<PO, P, NN, OFF>(oy, vb, o);
         const bool in0 = !BND || (r0 >= ox.first && r0 <= ox.last);
 #pragma unroll
         for (int r1 = 0; r1 < PO; ++r1) {
@@ -807,7 +818,8 @@ cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T*
                            cudaStream_t s) {
   if constexpr (DIM == 3 && sizeof(T) == 4) {
     if (use_int3<DIM, T>(g, b, x)) {
-      if (!BND && h->tuned_tile(1, level) == 1) return launch_int3<NN, T, BND, 1>(h, level, colour, b, x, g, s);
+      if constexpr (!BND)
+        if (h->tuned_tile(1, level) == 1) return launch_int3<NN, T, BND, 1>(h, level, colour, b, x, g, s);
       return launch_int3<NN, T, BND, 0>(h, level, colour, b, x, g, s);
     }
   }

@@ -261,8 +261,12 @@ def test_fcg_history_matches_oracle(case):
     assert np.allclose(h, hist, rtol=1e-6)
 
 
-def test_multi_rhs_and_graphs():
+def test_multi_rhs_and_graphs(monkeypatch):
     import torch
+    # the default launch rules on both handles (the autotuner may pick
+    # different launch paths for two handles, which round differently), so
+    # the graph replay must reproduce the direct launches bit for bit
+    monkeypatch.setenv("SIPG_AUTOTUNE", "0")
     dim, k, l2, nl = 3, 3, 3, 2
     N = 1 << l2
     for graphs in (0, 1):
