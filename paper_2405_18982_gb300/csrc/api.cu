@@ -596,6 +596,9 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
                "pinned host buffer");
   if (!h->side) {
     SIPG_CHECK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
+    int least = 0, greatest = 0;
+    SIPG_CHECK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range");
+    h->prio_hi = greatest;
     SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "event");
     SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");
   }

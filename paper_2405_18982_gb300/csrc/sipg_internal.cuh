@@ -119,6 +119,7 @@ struct sipg_handle {
   // from and joined to the calling stream with these events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int prio_hi = 0;  // greatest launch priority of the device: the interior kernel of a colour pass
   // host copies of the device-computed level constants (read back once at
   // bind time; kernels receive the small 1D operators as launch parameters)
   std::vector<LevelConst<double>> hc64;

@@ -427,11 +427,18 @@ cudaError_t launch_int3(const sipg_handle* h, int level, int colour, const T* b,
   }
   SmoothOps<C::PO, C::P, T, C::NT> ops;
   for (int t = 0; t < C::NT; ++t) make_ops<C::PO, C::P, BND, T>(h->hcst<T>(level), t, ops.t[t]);
-  dim3 grid((unsigned)((np + C::PPC - 1) / C::PPC), h->prm.nrhs);
-  smooth_int3_kernel<NN, T, BND, TILE><<<grid, C::THREADS, C::SMEM, s>>>(
-      ops, colour, b, x, h->lv[level].N, h->prm.smoother == SIPG_SMOOTHER_CONSISTENT ? 1 : 0,
-      (long long)h->lv[level].ndofs, g);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((np + C::PPC - 1) / C::PPC), h->prm.nrhs);
+  cfg.blockDim = dim3(C::THREADS);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute la[1];
+  la[0].id = cudaLaunchAttributePriority;
+  la[0].val.priority = h->prio_hi;
+  cfg.attrs = la;
+  cfg.numAttrs = BND ? 0 : 1;  // interior patches first (see the colour-pass dispatch)
+  return cudaLaunchKernelEx(&cfg, smooth_int3_kernel<NN, T, BND, TILE>, ops, colour, b, x, h->lv[level].N,
+                            h->prm.smoother == SIPG_SMOOTHER_CONSISTENT ? 1 : 0, (long long)h->lv[level].ndofs, g);
 }
 
 // The register-direct kernels take the 3D FP32 colour passes: their vector
