@@ -219,11 +219,11 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
                                   : (2 * P + (t - P * P) / P) * SA1 + PO * ((t - P * P) % P);
         T oa[PO];
         T(&vq)[P] = vin[q];
-        mass_rows1<PO, P, NN, OFF>(ox, vq, oa);
+        mass_rows2<PO, P, NN, OFF, false>(ox, vq, oa);
         i3_st_pairs<PO>(RA + dst, oa);
         if (t < P * P) {
           T ob[PO];
-          sipg_rows<PO, P, NN, OFF>(ox, vq, hl[q][0], hl[q][1], ob);
+          sipg_rows2<PO, P, NN, OFF>(ox, vq, hl[q][0], hl[q][1], ob);
           i3_st_pairs<PO>(RA + P * SA1 + dst, ob);
         }
       }
@@ -256,9 +256,9 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
             vb[a1] = RA[P * SA1 + SA1 * a1 + t];
           }
           const T h0 = RA[2 * P * SA1 + t], h1 = RA[(2 * P + 1) * SA1 + t];
-          mass_rows1<PO, P, NN, OFF>(oy, va, oc);
-          sipg_rows<PO, P, NN, OFF>(oy, va, h0, h1, od);
-          mass_rows1_acc<PO, P, NN, OFF>(oy, vb, od);
+          mass_rows2<PO, P, NN, OFF, false>(oy, va, oc);
+          sipg_rows2<PO, P, NN, OFF>(oy, va, h0, h1, od);
+          mass_rows2<PO, P, NN, OFF, true>(oy, vb, od);
 #pragma unroll
           for (int r1 = 0; r1 < PO; ++r1) {
             Cc[SC * a2 + PO * r1 + r0] = oc[r1];
@@ -269,7 +269,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
           T vz[P], oc[PO];
 #pragma unroll
           for (int a1 = 0; a1 < P; ++a1) vz[a1] = RA[(2 * P + 2 + side) * SA1 + PO * a1 + r0];
-          mass_rows1<PO, P, NN, OFF>(oy, vz, oc);
+          mass_rows2<PO, P, NN, OFF, false>(oy, vz, oc);
 #pragma unroll
           for (int r1 = 0; r1 < PO; ++r1) CZ[side * CZS + PO * r1 + r0] = oc[r1];
         }
@@ -309,14 +309,14 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
         vc[a2] = Cc[SC * a2 + lane];
         vd[a2] = Dd[SC * a2 + lane];
       }
-      sipg_rows<PO, P, NN, OFF>(oz, vc, CZ[lane], CZ[CZS + lane], o);
-      mass_rows1_acc<PO, P, NN, OFF>(oz, vd, o);
+      sipg_rows2<PO, P, NN, OFF>(oz, vc, CZ[lane], CZ[CZS + lane], o);
+      mass_rows2<PO, P, NN, OFF, true>(oz, vd, o);
 #pragma unroll
       for (int r2 = 0; r2 < PO; ++r2) {
         const bool in = inxy && r2 >= zlo && r2 <= zhi;
         o[r2] = in ? bv[r2] - o[r2] : T(0);
       }
-      st_rows<PO>(oz.S, o, t1);
+      st_rows2<PO>(oz.S2, o, t1);
 #pragma unroll
       for (int k2 = 0; k2 < PO; ++k2) RA[ST * r1 + PO * k2 + r0] = t1[k2];
     });
@@ -331,7 +331,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       T w[PO], o[PO];
 #pragma unroll
       for (int j = 0; j < PO; ++j) w[j] = RA[ST * j + lane];
-      st_rows<PO>(oy.S, w, o);
+      st_rows2<PO>(oy.S2, w, o);
 #pragma unroll
       for (int k1 = 0; k1 < PO; ++k1) RB[SQ * r0 + PO * r1 + k1] = o[k1];  // r1 here = k2
     });
@@ -347,7 +347,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       T w[PO], o[PO];
 #pragma unroll
       for (int j = 0; j < PO; ++j) w[j] = RB[SQ * j + lane];
-      st_rows<PO>(ox.S, w, o);
+      st_rows2<PO>(ox.S2, w, o);
       if (BND) {
 #pragma unroll
         for (int k0 = 0; k0 < PO; ++k0) o[k0] = o[k0] / (ox.lam[k0] + lyz);
@@ -355,7 +355,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
 #pragma unroll
         for (int k0 = 0; k0 < PO; ++k0) o[k0] *= dinv[k0 * PO * PO + lane];
       }
-      s_rows<PO>(ox.S, o, w);
+      s_rows2<PO>(ox.St2, o, w);
 #pragma unroll
       for (int j = 0; j < PO; ++j) RA[SQ * r0 + PO * r1 + j] = w[j];
     });
@@ -369,7 +369,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       T w[PO], o[PO];
 #pragma unroll
       for (int j = 0; j < PO; ++j) w[j] = RA[SQ * j + lane];
-      s_rows<PO>(oy.S, w, o);
+      s_rows2<PO>(oy.St2, w, o);
 #pragma unroll
       for (int j = 0; j < PO; ++j) RB[ST * j + lane] = o[j];
     });
@@ -388,7 +388,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       }
 #pragma unroll
       for (int k2 = 0; k2 < PO; ++k2) w[k2] = RB[ST * r1 + PO * k2 + r0];
-      s_rows<PO>(oz.S, w, o);
+      s_rows2<PO>(oz.St2, w, o);
 #pragma unroll
       for (int r2 = 0; r2 < PO; ++r2) {
         const bool in = inxy && r2 >= zlo && r2 <= zhi;

@@ -81,6 +81,14 @@ struct Ops1D {
   T S[PO * PO];   // S[j][i]: row j, column i (column i = eigenvector i)
   T lam[PO];
   int first, last;  // rows of V_j are [first, last] (patch-node numbering minus OFF)
+  // FP32: the same operators as pairs of consecutive rows (outputs), for the
+  // packed two-lane FMA of sm_100+: one instruction computes two outputs
+  static constexpr int NP = sizeof(T) == 4 ? 1 : 0;
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  T2 S2[NP ? PO * PO / 2 : 1];   // S2[j][q] = (S[j][2q], S[j][2q+1])      (S^T rows)
+  T2 St2[NP ? PO * PO / 2 : 1];  // St2[q][j] = (S[2q][j], S[2q+1][j])     (S rows)
+  T2 L2[NP ? PO * P / 2 : 1];    // L2[q][c] = (Lm[2q][c], Lm[2q+1][c])
+  T2 mw2[NP ? PO / 2 : 1], mu2[NP ? PO / 2 : 1];
 };
 
 template <int DIM, int NN, bool BND, typename T>
@@ -173,6 +181,79 @@ __device__ __forceinline__ void s_rows(const T* __restrict__ S, const T (&v)[PO]
   }
 }
 
+// Packed FP32 (two outputs per FMA instruction) versions of the line
+// contractions; same products and summation order per output as the scalar
+// ones, so the results are bitwise equal.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+template <int PO>
+__device__ __forceinline__ void st_rows2(const float2* __restrict__ S2, const float (&v)[PO], float (&o)[PO]) {
+#pragma unroll
+  for (int q = 0; q < PO / 2; ++q) {
+    float2 s = __fmul2_rn(S2[q], bc2(v[0]));
+#pragma unroll
+    for (int j = 1; j < PO; ++j) s = __ffma2_rn(S2[j * (PO / 2) + q], bc2(v[j]), s);
+    o[2 * q] = s.x;
+    o[2 * q + 1] = s.y;
+  }
+}
+
+template <int PO>
+__device__ __forceinline__ void s_rows2(const float2* __restrict__ St2, const float (&v)[PO], float (&o)[PO]) {
+#pragma unroll
+  for (int q = 0; q < PO / 2; ++q) {
+    float2 s = __fmul2_rn(St2[q * PO], bc2(v[0]));
+#pragma unroll
+    for (int j = 1; j < PO; ++j) s = __ffma2_rn(St2[q * PO + j], bc2(v[j]), s);
+    o[2 * q] = s.x;
+    o[2 * q + 1] = s.y;
+  }
+}
+
+// rows 2q, 2q+1 of the SIPG rows over the union of their structural nonzeros
+// (a column that is a structural zero of one row carries an exact 0 there)
+template <int PO, int P, int NN, int OFF>
+__device__ __forceinline__ void sipg_rows2(const Ops1D<PO, P, float>& op, const float (&v)[P], float h0, float h1,
+                                           float (&o)[PO]) {
+#pragma unroll
+  for (int q = 0; q < PO / 2; ++q) {
+    const int a0 = 2 * q + OFF, a1 = a0 + 1;
+    float2 s = make_float2((a0 < NN) ? op.hlo[2 * q] * h0 : op.hhi[2 * q] * h1,
+                           (a1 < NN) ? op.hlo[2 * q + 1] * h0 : op.hhi[2 * q + 1] * h1);
+#pragma unroll
+    for (int c = 0; c < P; ++c)
+      if (lr_nz<NN>(a0, c) || lr_nz<NN>(a1, c)) s = __ffma2_rn(op.L2[q * P + c], bc2(v[c]), s);
+    o[2 * q] = s.x;
+    o[2 * q + 1] = s.y;
+  }
+}
+
+template <int PO, int P, int NN, int OFF, bool ACC>
+__device__ __forceinline__ void mass_rows2(const Ops1D<PO, P, float>& op, const float (&v)[P], float (&o)[PO]) {
+  float sc[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    float a = op.ma[0] * v[c * NN];
+#pragma unroll
+    for (int j = 1; j < NN; ++j) a = fmaf(op.ma[j], v[c * NN + j], a);
+    sc[c] = a;
+  }
+#pragma unroll
+  for (int q = 0; q < PO / 2; ++q) {
+    const int a0 = 2 * q + OFF, a1 = a0 + 1;
+    const float2 vv = make_float2(v[a0], v[a1]);
+    const float2 ss = make_float2(sc[a0 / NN], sc[a1 / NN]);
+    float2 t;
+    if (ACC)
+      t = __ffma2_rn(op.mw2[q], vv, make_float2(o[2 * q], o[2 * q + 1]));
+    else
+      t = __fmul2_rn(op.mw2[q], vv);
+    t = __ffma2_rn(op.mu2[q], ss, t);
+    o[2 * q] = t.x;
+    o[2 * q + 1] = t.y;
+  }
+}
+
 template <int L, typename T>
 __device__ __forceinline__ void ld(const T* p, int stride, T (&v)[L]) {
 #pragma unroll
@@ -242,6 +323,17 @@ void make_ops(const LevelConst<T>& lc, int t, Ops1D<PO, P, T>& op) {
     }
   op.first = BND ? first : 0;
   op.last = BND ? first + p - 1 : PO - 1;
+  if constexpr (sizeof(T) == 4) {
+    for (int q = 0; q < PO / 2; ++q) {
+      for (int j = 0; j < PO; ++j) {
+        op.S2[j * (PO / 2) + q] = make_float2(op.S[j * PO + 2 * q], op.S[j * PO + 2 * q + 1]);
+        op.St2[q * PO + j] = make_float2(op.S[2 * q * PO + j], op.S[(2 * q + 1) * PO + j]);
+      }
+      for (int c = 0; c < P; ++c) op.L2[q * P + c] = make_float2(op.Lm[2 * q * P + c], op.Lm[(2 * q + 1) * P + c]);
+      op.mw2[q] = make_float2(op.mw[2 * q], op.mw[2 * q + 1]);
+      op.mu2[q] = make_float2(op.mu[2 * q], op.mu[2 * q + 1]);
+    }
+  }
 }
 
 // patch enumeration of colour c: per direction m in [0, cnt), v = 2m+1 (odd
