@@ -903,11 +903,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
 }
 
 #include "smooth_int3.cuh"
+#include "smooth_int2.cuh"
 #include "smooth_w3.cuh"
 
 template <int DIM, int NN, bool BND, typename T>
 cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T* b, T* x, const PatchGrid& g,
                            cudaStream_t s) {
+  if constexpr (DIM == 2 && sizeof(T) == 4) {
+    if (g.n_int < (1LL << 31) && (reinterpret_cast<uintptr_t>(b) % 16) == 0 &&
+        (reinterpret_cast<uintptr_t>(x) % 16) == 0)
+      return launch_int2<NN, T, BND>(h, level, colour, b, x, g, s);
+  }
   if constexpr (DIM == 3 && sizeof(T) == 4) {
     if (use_int3<DIM, T>(g, b, x)) {
       if constexpr (!BND)
