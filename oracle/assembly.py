@@ -7,7 +7,7 @@ Generic d-dimensional quadrature assembly; it does NOT use the Kronecker
 structure of Sec. 2.2 (that structure is what ``oracle.direct`` builds
 independently, and the two are compared in the tests).
 
-Conventions (readings of the paper, all listed in the design doc):
+Conventions (readings of the paper where it is garbled or silent):
   * jump on an interior face: [[u]] = u^- n^- + u^+ n^+ (Eq. jump_mean prints
     "(u^+ + u^-) n^+", read as the standard SIPG jump); mean {g} = (g^- + g^+)/2;
   * boundary face: [[u]] = u n, {grad u} = grad u (Eq. jump_boundary);

@@ -4,7 +4,7 @@ local-solver; Sec. 3.3 for the iteration count nu).
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Readings of the paper (listed in the design doc):
+Readings of the paper (where it is silent or ambiguous):
   * level l has N_l = N_L / 2^(L-l) cells per direction; the coarsest level
     is solved exactly (P_0^{-1} = A_0^{-1}, Sec. 3);
   * coarse operators are re-discretised SIPG matrices with their own h;
