@@ -79,7 +79,9 @@ typedef enum {
    * the cells around the patch (default; symmetric V-cycle). */
   SIPG_SMOOTHER_CONSISTENT = 0,
   /* r_j = R_j b - Abar_j Rbar_j x with only the patch cells (the paper's
-   * Dirichlet kernel, inconsistent residual). */
+   * Dirichlet kernel, inconsistent residual): Abar_j is the form on the
+   * patch cells in which the last face term -[[u]].{grad v} of the
+   * patch-boundary faces inside the domain is left out (Sec. 3.1). */
   SIPG_SMOOTHER_PAPER = 1
 } sipg_smoother;
 

@@ -91,7 +91,7 @@ def _face_points(dim, k, e, s):
     return pts, tw
 
 
-def face_matrices(dim, k, N, gamma, penalty_only=False):
+def face_matrices(dim, k, N, gamma, penalty_only=False, drop_last=False):
     """Face blocks of the SIPG form (Eq. bilinear_form) for every direction e.
 
     Returns a dict with, for each e:
@@ -100,7 +100,9 @@ def face_matrices(dim, k, N, gamma, penalty_only=False):
       ('bnd', e, s): block of a boundary face at y_e = s (s = 0: x_e = 0,
                   outward normal -e_e; s = 1: x_e = 1, normal +e_e).
     Entry [I, J] = int_F gamma [[phi_J]].[[phi_I]] - {grad phi_J}.[[phi_I]]
-                   - [[phi_J]].{grad phi_I}  (or only the first term).
+                   - [[phi_J]].{grad phi_I}  (or only the first term; with
+    ``drop_last`` the first two, i.e. the last face term of Eq. bilinear_form
+    left out).
     """
     h = 1.0 / N
     jac = h ** (dim - 1)
@@ -124,7 +126,7 @@ def face_matrices(dim, k, N, gamma, penalty_only=False):
                     B[Y][X] = jac * pen
                 else:
                     flux = np.einsum("q,qje,qie->ij", w, avg[X], jump[Y])
-                    sym = np.einsum("q,qje,qie->ij", w, jump[X], avg[Y])
+                    sym = 0.0 if drop_last else np.einsum("q,qje,qie->ij", w, jump[X], avg[Y])
                     B[Y][X] = jac * (pen - flux - sym)
         out[("int", e)] = B
         for s in (0, 1):
@@ -137,7 +139,7 @@ def face_matrices(dim, k, N, gamma, penalty_only=False):
                 out[("bnd", e, s)] = jac * pen
             else:
                 flux = np.einsum("q,qje,qie->ij", w, G, jmp)
-                sym = np.einsum("q,qje,qie->ij", w, jmp, G)
+                sym = 0.0 if drop_last else np.einsum("q,qje,qie->ij", w, jmp, G)
                 out[("bnd", e, s)] = jac * (pen - flux - sym)
     return out
 
@@ -147,11 +149,13 @@ def element_blocks(dim, k, N, kappa=1.0, eta=1.0, part="full"):
 
     part = "full": the whole form; "penalty": only sum_F int_F [[u]].[[v]]
     with gamma = 1 (the derivative of the form with respect to a uniform face
-    penalty value), still multiplied by kappa."""
+    penalty value), still multiplied by kappa; "no_last": the whole form
+    without the last face term -[[u]].{grad v} (the face blocks the paper's
+    Dirichlet kernel keeps on patch-boundary faces, Sec. 3.1)."""
     gamma = penalty(k, N, eta)
-    if part == "full":
+    if part in ("full", "no_last"):
         K, _ = cell_matrices(dim, k, N)
-        F = face_matrices(dim, k, N, gamma)
+        F = face_matrices(dim, k, N, gamma, drop_last=(part == "no_last"))
     elif part == "penalty":
         n = k + 1
         K = np.zeros((n ** dim, n ** dim))
@@ -236,13 +240,21 @@ def block_apply(dim, k, N, blocks, x, cells_sel=None):
     return y
 
 
-def principal_block(dim, k, N, blocks, cells_sel):
+def principal_block(dim, k, N, blocks, cells_sel, outer=None):
     """Dense A[D, D] for D = all DoFs of the listed cells (flat cell numbers,
     in the given order, n^d DoFs each), from the element blocks: a cell's
     diagonal block is its cell block plus the self parts of its faces; two
     listed cells sharing a face couple through that face's off-diagonal block.
     For the vertex-patch cells this is the patch matrix of Sec. 3.1 before
-    restriction to V_j, on meshes too large to assemble."""
+    restriction to V_j, on meshes too large to assemble.
+
+    ``outer``: element blocks used instead of ``blocks`` for the self part of
+    a face whose other cell is NOT listed (an interior mesh face on the
+    boundary of the selection); faces on the domain boundary keep ``blocks``.
+    With ``element_blocks(..., part="no_last")`` this gives the patch operator
+    of the paper's Dirichlet kernel (Sec. 3.1)."""
+    if outer is None:
+        outer = blocks
     n = k + 1
     nl = n ** dim
     allc = cell_multi_index(dim, N)
@@ -256,17 +268,21 @@ def principal_block(dim, k, N, blocks, cells_sel):
         for e in range(dim):
             B = blocks[("int", e)]
             if cm[e] > 0:
-                D += B[1][1]
                 j = pos.get(c - int(strides[e]))
                 if j is not None:
+                    D += B[1][1]
                     out[i * nl:(i + 1) * nl, j * nl:(j + 1) * nl] += B[1][0]
+                else:
+                    D += outer[("int", e)][1][1]
             else:
                 D += blocks[("bnd", e, 0)]
             if cm[e] < N - 1:
-                D += B[0][0]
                 j = pos.get(c + int(strides[e]))
                 if j is not None:
+                    D += B[0][0]
                     out[i * nl:(i + 1) * nl, j * nl:(j + 1) * nl] += B[0][1]
+                else:
+                    D += outer[("int", e)][0][0]
             else:
                 D += blocks[("bnd", e, 1)]
         out[i * nl:(i + 1) * nl, i * nl:(i + 1) * nl] += D

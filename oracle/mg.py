@@ -17,18 +17,26 @@ Readings of the paper (where it is silent or ambiguous):
     nodes on the patch boundary (Sec. 3.1); a patch-boundary end that lies on
     the domain boundary is kept in V_j (the paper is silent);
   * "consistent" local residual r_j = R_j (b - A x) (default), or the paper's
-    Dirichlet-kernel residual r_j = R_j b - Abar_j Rbar_j x with only the patch
-    cells in the domain of dependence ("paper");
+    Dirichlet-kernel residual r_j = R_j b - Abar_j Rbar_j x ("paper"): Abar_j
+    is the form on the patch cells alone (cell terms, all terms of the faces
+    between patch cells and on the domain boundary) in which the last face
+    term -[[u]].{grad v} of the patch-boundary faces inside the domain is
+    left out.  Sec. 3.1 states that this term does not vanish for v in V_j
+    and that ignoring it makes the residual inconsistent; keeping its
+    patch-side half instead gives iteration counts that grow with the level,
+    unlike Table 2;
   * colours: c = sum_e (v_e mod 2) 2^e for vertex index v; pre-smoothing visits
     colours 0..2^d-1, post-smoothing visits them in reverse;
   * outer solver: flexible CG with beta = <z_{i+1}, r_{i+1} - r_i> / <z_i, r_i>,
-    stopped at ||r||_2 / ||b||_2 <= rtol (Euclidean norm, Sec. 3.3).
+    stopped at ||r||_2 / ||b||_2 <= rtol (Euclidean norm, Sec. 3.3), or the
+    paper's GMRES (Sec. 3.3, Tables 1 and 2), preconditioned from the right so
+    that its residual is the Euclidean residual of Ax = b.
 """
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-from .assembly import assemble
+from .assembly import assemble, element_blocks, principal_block
 from .basis import gauss_lobatto, lagrange_values, tensor_index
 from .layout import cell_multi_index, dof_index
 
@@ -74,6 +82,8 @@ def vertex_patches(dim, k, N, variant="consistent"):
       V       : sorted global DoF indices of the Dirichlet-kernel space V_j
       dofs    : all DoF indices of the 2^d patch cells (domain of dependence
                 of the paper's Dirichlet kernel)
+      cells   : the flat numbers of the 2^d patch cells, ascending (their DoFs
+                in this order are ``dofs``)
       type    : per direction (v_e == 1, v_e == N-1)
     """
     n = k + 1
@@ -82,9 +92,10 @@ def vertex_patches(dim, k, N, variant="consistent"):
     offsets = tensor_index(dim, 2)
     patches = []
     for v in tensor_index(dim, N - 1) + 1:
-        keepV, alld = [], []
+        keepV, alld, cells = [], [], []
         for o in offsets:
             cell = v - 1 + o
+            cells.append(int(sum(int(cell[e]) * N ** e for e in range(dim))))
             g = dof_index(dim, N, n, cell[None, :], np.arange(nloc))
             a = o[None, :] * n + loc                  # 1D patch coordinates 0..2n-1
             inside = np.ones(nloc, dtype=bool)
@@ -99,6 +110,7 @@ def vertex_patches(dim, k, N, variant="consistent"):
             colour=int(sum((int(v[e]) % 2) << e for e in range(dim))),
             V=np.sort(np.concatenate(keepV)),
             dofs=np.sort(np.concatenate(alld)),
+            cells=sorted(cells),
             type=tuple((bool(v[e] == 1), bool(v[e] == N - 1)) for e in range(dim)),
         ))
     return patches
@@ -113,6 +125,9 @@ class Level:
         self.A = assemble(dim, k, N, kappa, eta)
         self.ndof = self.A.shape[0]
         self.patches = vertex_patches(dim, k, N)
+        if variant == "paper":
+            full = element_blocks(dim, k, N, kappa, eta)
+            no_last = element_blocks(dim, k, N, kappa, eta, part="no_last")
         for p in self.patches:
             V = p["V"]
             Aj = self.A[V][:, V].toarray()           # A_j = R_j A R_j^T
@@ -121,7 +136,10 @@ class Level:
                 p["rows"] = self.A[V]                # all columns: R_j A
                 p["cols"] = None
             elif variant == "paper":
-                p["rows"] = self.A[V][:, p["dofs"]]  # Abar_j: patch columns only
+                # Abar_j over the patch cells, rows V_j: the last face term
+                # dropped on the patch-boundary faces inside the domain
+                Abar = principal_block(dim, k, N, full, p["cells"], outer=no_last)
+                p["rows"] = Abar[np.searchsorted(p["dofs"], V)]
                 p["cols"] = p["dofs"]
             else:
                 raise ValueError(variant)
@@ -229,6 +247,68 @@ def fcg(A_apply, precond, b, rtol=1e-10, maxit=200, x0=None):
         p = z_new + beta * p
         r, z = r_new, z_new
         rz = r @ z
+    return x, hist
+
+
+def gmres(A_apply, precond, b, rtol=1e-8, maxit=200, restart=30, x0=None):
+    """GMRES preconditioned from the right in its flexible form (the
+    preconditioned directions z_j = B v_j are kept, so B may vary between
+    steps; for a fixed B this is right-preconditioned GMRES).  Arnoldi with
+    modified Gram-Schmidt builds an orthonormal basis v_1..v_{j+1} with
+    A z_j = sum_i h_ij v_i; plane rotations reduce the Hessenberg matrix to
+    triangular form, so that |g_{j+1}| is the Euclidean norm of b - A x_j for
+    the x_j = x_0 + Z_j y_j minimising it.  A cycle ends after ``restart``
+    steps or when that norm reaches rtol ||b||_2; then x is updated and the
+    true residual b - A x recomputed (it replaces the last history entry):
+    the solve stops when it is <= rtol ||b||_2, else GMRES restarts from x.
+    Returns (x, history of ||r||_2), the history starting with ||r_0||."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    r = b - A_apply(x)
+    hist = [np.linalg.norm(r)]
+    if bnorm == 0.0 or hist[0] <= rtol * bnorm:
+        return x, hist
+    steps = 0
+    while steps < maxit:
+        beta = np.linalg.norm(r)
+        m = min(restart, maxit - steps)
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m))
+        g = np.zeros(m + 1)
+        g[0] = beta
+        cs, sn = np.zeros(m), np.zeros(m)
+        j = 0
+        while j < m:
+            Z.append(precond(V[j]))
+            w = A_apply(Z[j])
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            hn = H[j + 1, j] = np.linalg.norm(w)
+            V.append(w / hn if hn > 0.0 else w)
+            for i in range(j):                       # earlier rotations
+                a, c = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * c
+                H[i + 1, j] = -sn[i] * a + cs[i] * c
+            den = np.hypot(H[j, j], H[j + 1, j])      # new rotation
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j], H[j + 1, j] = den, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            j += 1
+            steps += 1
+            hist.append(abs(g[j]))
+            if hist[-1] <= rtol * bnorm or hn == 0.0:   # converged, or exact
+                break
+        y = sla.solve_triangular(H[:j, :j], g[:j])
+        for i in range(j):
+            x = x + y[i] * Z[i]
+        r = b - A_apply(x)
+        hist[-1] = np.linalg.norm(r)   # the true residual ends every cycle
+        if hist[-1] <= rtol * bnorm:
+            break
     return x, hist
 
 

@@ -282,7 +282,8 @@ __device__ double l_hi_entry(const LevelConst<double>& c, int k, int i, int j) {
 }
 
 __global__ void setup_levels_kernel(LevelConst<double>* out, int k, int N_finest, int n_levels,
-                                    double kappa, double eta, double* scratch, int* status) {
+                                    double kappa, double eta, int paper_residual, double* scratch,
+                                    int* status) {
   const int l = blockIdx.x;
   const int L = n_levels - 1;
   const int n = k + 1;
@@ -356,8 +357,20 @@ __global__ void setup_levels_kernel(LevelConst<double>* out, int k, int N_finest
         c.Mr[t][r][1 + b] = Mp[a][b];
       }
       // halo: face node k of cell v-2 (low) and node 0 of cell v+1 (high)
-      c.Lr[t][r][0] = (!(t & 1) && a < n) ? l_lo_entry(c, k, a, k) : 0.0;
-      c.Lr[t][r][P + 1] = (!(t & 2) && a >= n) ? l_hi_entry(c, k, a - n, 0) : 0.0;
+      double hlo = (!(t & 1) && a < n) ? l_lo_entry(c, k, a, k) : 0.0;
+      double hhi = (!(t & 2) && a >= n) ? l_hi_entry(c, k, a - n, 0) : 0.0;
+      if (paper_residual) {
+        // Dirichlet kernel (Sec. 3.1): the last face term -[[u]].{grad v} of
+        // a patch-boundary face inside the domain is left out.  For rows in
+        // V_j it couples only the two face nodes, with opposite coefficients
+        // (the jump of a constant vanishes), so leaving it out adds the halo
+        // coefficient to the patch end node's column and drops the halo.
+        c.Lr[t][r][1] += hlo;
+        c.Lr[t][r][P] += hhi;
+        hlo = hhi = 0.0;
+      }
+      c.Lr[t][r][0] = hlo;
+      c.Lr[t][r][P + 1] = hhi;
     }
     double As[SIPG_MAXP * SIPG_MAXP], Bs[SIPG_MAXP * SIPG_MAXP];
     double Ss[SIPG_MAXP * SIPG_MAXP], W1[SIPG_MAXP * SIPG_MAXP], W2[SIPG_MAXP * SIPG_MAXP];
@@ -464,7 +477,8 @@ cudaError_t launch_setup(sipg_handle* h, cudaStream_t s) {
   double* scratch = reinterpret_cast<double*>(h->ws + h->off_scratch_setup + 256);
   cudaMemsetAsync(status, 0, sizeof(int), s);
   setup_levels_kernel<<<nl, 32, 0, s>>>(h->c64(0), h->prm.degree, 1 << h->prm.log2_cells, nl,
-                                        h->prm.kappa, h->prm.penalty_factor, scratch, status);
+                                        h->prm.kappa, h->prm.penalty_factor,
+                                        h->prm.smoother == SIPG_SMOOTHER_PAPER ? 1 : 0, scratch, status);
   constants_to_float_kernel<<<nl, 256, 0, s>>>(h->c64(0), h->c32(0));
   h->launches += 2;
   return cudaGetLastError();
