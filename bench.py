@@ -573,6 +573,54 @@ def run_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_table2(args):
+    """--mode table2: the setting of the paper's Table 2 (Dirichlet kernel) on
+    the device: 3D unit cube, f = 1, 2^L cells per direction down to 2^3 on
+    the coarsest level, GMRES to 1e-8 preconditioned from the right by one
+    V-cycle whose smoother uses the Dirichlet-kernel residual; nu (Sec. 3.3),
+    steps and time to solution with the FP64 and the FP32 V-cycle, the
+    consistent residual beside it, and the value printed in Table 2.  Cases
+    k = 3..7, L = 2..7 up to --max-dofs DoFs.  One JSON line per case."""
+    import time
+
+    import numpy as np
+    import torch
+    import paper_2405_18982_gb300 as pkg
+    from paper_2405_18982_gb300 import (SIPG, SIPG_FP32, SIPG_FP64, SIPG_SMOOTHER_CONSISTENT,
+                                        SIPG_SMOOTHER_PAPER, Params)
+    pkg.load(pkg.build())
+    printed = np.loadtxt(os.path.join(ROOT, "tests", "golden", "table2_dirichlet_nu.txt"))
+    for L in range(2, 8):
+        for k in range(3, 8):
+            n = (1 << L) ** 3 * (k + 1) ** 3
+            if n > args.max_dofs:
+                continue
+            row = {"mode": "table2", "degree": k, "L": L, "dofs": n,
+                   "nu_table2": None if np.isnan(printed[L - 2, k - 2]) else float(printed[L - 2, k - 2])}
+            for tag, prec, sm in (("fp64", SIPG_FP64, SIPG_SMOOTHER_PAPER), ("mixed", SIPG_FP32, SIPG_SMOOTHER_PAPER),
+                                  ("consistent_mixed", SIPG_FP32, SIPG_SMOOTHER_CONSISTENT)):
+                s = SIPG(Params(dim=3, degree=k, log2_cells=L, n_levels=L, vcycle_precision=prec, smoother=sm))
+                f = torch.ones(1, s.ndofs(), dtype=torch.float64, device="cuda")
+                b = torch.zeros_like(f)
+                s.rhs(f, b)
+                x = torch.zeros_like(b)
+                work = torch.empty(s.gmres_workspace_bytes(30) + 256, dtype=torch.uint8, device="cuda")
+                s.gmres_solve(b, x, rtol=1e-8, maxit=100, restart=30, work=work)   # warm-up
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = s.gmres_solve(b, x, rtol=1e-8, maxit=100, restart=30, work=work)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                row[f"nu_{tag}"] = round(info.nu, 2)
+                row[f"steps_{tag}"] = info.iterations
+                row[f"time_to_1e-8_{tag}_ms"] = round(dt * 1e3, 2)
+                s.close()
+                del s, work, f, b, x
+                torch.cuda.empty_cache()
+            print(json.dumps(row), flush=True)
+
+
 # ----------------------------------------------------------------- oracle arm
 SAMPLE = (3, 3, 8, 3)   # dim, k, N, levels: the same discretisation on 8^3 cells
 
@@ -650,7 +698,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep"])
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep", "table2"])
+    ap.add_argument("--max-dofs", type=float, default=2e7, help="largest case of --mode table2")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
@@ -659,6 +709,8 @@ def main():
         run_batched(args)
     elif args.mode == "sweep":
         run_sweep(args)
+    elif args.mode == "table2":
+        run_table2(args)
     elif args.mode != "solve":
         run_kernel_only(args)
     else:

@@ -31,9 +31,9 @@
  * entry point allocates device memory.  Vector arguments are device pointers
  * unless stated otherwise, must be 16-byte aligned and must not alias unless
  * stated.  `stream` is a cudaStream_t (NULL = legacy default stream); all work
- * is ordered on it.  Only sipg_solve, sipg_adjoint_solve and
- * sipg_solve_host synchronise (their stream), because convergence is decided
- * on the host.
+ * is ordered on it.  Only sipg_solve, sipg_adjoint_solve, sipg_solve_host
+ * and sipg_gmres_solve synchronise (their stream), because convergence is
+ * decided on the host.
  *
  * Errors: every call returns a sipg_status; failures never abort or trap.
  * sipg_last_error(h) returns a message for the last failure on h.
@@ -192,6 +192,35 @@ sipg_status sipg_adjoint_solve(sipg_handle* h, const double* g, double* lambda, 
  * out, all on `stream`.  Synchronises stream. */
 sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host, double rtol,
                             int maxit, sipg_info* info, void* stream);
+
+/* Largest GMRES restart length (Krylov vectors kept per cycle). */
+#define SIPG_GMRES_MAX_RESTART 64
+
+/* Device bytes that sipg_gmres_solve needs for restart length `restart`
+ * (1..SIPG_GMRES_MAX_RESTART): restart+1 Arnoldi vectors, restart
+ * preconditioned vectors (FP64, finest level, one right-hand side each) and
+ * reduction scratch.  0 for a bad argument.  No GPU needed. */
+size_t sipg_gmres_workspace_bytes(const sipg_handle* h, int restart);
+/* GMRES, the paper's outer solver (Sec. 3.3, Tables 1 and 2), on the finest
+ * level, preconditioned from the right by one V-cycle (params.vcycle_precision)
+ * in flexible form: the preconditioned directions are stored, so the FP32
+ * V-cycle may serve as preconditioner.  Arnoldi with classical Gram-Schmidt
+ * applied twice; plane rotations give ||b - A x||_2 after every step; a cycle
+ * ends after `restart` steps or at ||b - A x||_2 <= rtol ||b||_2, then x is
+ * updated and the true residual recomputed (it ends the history of the
+ * cycle); the solve stops once that is <= rtol ||b||_2 or after maxit steps,
+ * else restarts from x.  With params.smoother = SIPG_SMOOTHER_PAPER this is
+ * the setting of Table 2 (Dirichlet kernel).  b, x: FP64, one column (nrhs
+ * must be 1, else SIPG_EUNSUPPORTED); x holds the initial guess on entry.
+ * work: caller-owned device memory of at least
+ * sipg_gmres_workspace_bytes(h, restart) bytes, 256-byte aligned, not shared
+ * with any other argument.  info->iterations counts GMRES steps (V-cycles);
+ * info->nu is computed from the history as for sipg_solve.  Returns
+ * SIPG_ENOCONV after maxit steps, SIPG_EBREAKDOWN on a non-finite scalar.
+ * Synchronises stream (after every step: the Hessenberg matrix is kept on
+ * the host). */
+sipg_status sipg_gmres_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
+                             int restart, void* work, size_t work_bytes, sipg_info* info, void* stream);
 
 /* out[r] = <a_r, b_r> for every column r (FP64, deterministic order),
  * written to device memory. */

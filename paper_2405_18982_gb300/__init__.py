@@ -195,6 +195,30 @@ class SIPG:
     def adjoint_solve(self, g, lam, rtol=1e-10, maxit=200, stream=None, history=256, allow_noconv=False):
         return self._solve(self.lib.sipg_adjoint_solve, g, lam, rtol, maxit, stream, history, allow_noconv)
 
+    def gmres_workspace_bytes(self, restart=30):
+        return int(self.lib.sipg_gmres_workspace_bytes(self.h, restart))
+
+    def gmres_solve(self, b, x, rtol=1e-8, maxit=200, restart=30, stream=None, history=256,
+                    allow_noconv=False, work=None):
+        """GMRES preconditioned from the right by the V-cycle (the paper's
+        outer solver); ``work`` (a CUDA uint8 tensor) is allocated here when
+        not given or too small."""
+        import torch
+        nbytes = self.gmres_workspace_bytes(restart)
+        if nbytes == 0:
+            raise SipgError(B.SIPG_EINVAL, f"restart {restart} out of range")
+        if work is None or work.numel() < nbytes + 256:
+            work = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (work.data_ptr() + 255) & ~255
+        hist = (ctypes.c_double * history)()
+        info = B.sipg_info(0, 0, 0.0, 0.0, hist, history, 0)
+        st = self.lib.sipg_gmres_solve(self.h, _ptr(b), _ptr(x), rtol, maxit, restart, ctypes.c_void_p(aligned),
+                                       nbytes, ctypes.byref(info), self._stream(stream))
+        if st != 0 and not (allow_noconv and st == B.SIPG_ENOCONV):
+            self._check(st)
+        return SolveInfo(info.iterations, info.status, info.rel_residual, info.nu,
+                         [hist[i] for i in range(info.history_len)])
+
     def solve_host(self, f_host, u_host, rtol=1e-10, maxit=200, stream=None, history=256):
         """f_host, u_host: CPU float64 tensors (pinned for async copies)."""
         if f_host.is_cuda or u_host.is_cuda:

@@ -26,6 +26,7 @@ SIPG_FP64 = 0
 SIPG_FP32 = 1
 SIPG_SMOOTHER_CONSISTENT = 0
 SIPG_SMOOTHER_PAPER = 1
+SIPG_GMRES_MAX_RESTART = 64
 
 
 class sipg_params(ctypes.Structure):
@@ -71,6 +72,9 @@ SIGNATURES = {
     "sipg_solve": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
     "sipg_adjoint_solve": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
     "sipg_solve_host": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
+    "sipg_gmres_workspace_bytes": (ctypes.c_size_t, [_vp, _i]),
+    "sipg_gmres_solve": (_st, [_vp, _vp, _vp, _d, _i, _i, _vp, ctypes.c_size_t,
+                               ctypes.POINTER(sipg_info), _vp]),
     "sipg_dot": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_dot_noalloc": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_selftest_barrier": (_st, [_vp, _i, _vp]),

@@ -370,6 +370,196 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
   return finish(runs[0]);
 }
 
+// ------------------------------------------------------------------ GMRES
+// Caller-owned workspace of sipg_gmres_solve: Arnoldi vectors V_0..V_m and
+// preconditioned vectors Z_0..Z_{m-1} (finest level, FP64, each 256-byte
+// aligned), reduction partials for m+1 simultaneous dot products, m+1
+// device scalars.
+struct GmresLayout {
+  size_t vec = 0, off_z = 0, off_part = 0, off_dev = 0, total = 0;
+};
+
+GmresLayout gmres_layout(const sipg_handle* h, int m) {
+  GmresLayout g;
+  g.vec = align256(h->lv[h->L].ndofs * sizeof(double));
+  g.off_z = (size_t)(m + 1) * g.vec;
+  g.off_part = g.off_z + (size_t)m * g.vec;
+  g.off_dev = g.off_part + align256(sizeof(double) * (size_t)(m + 1) * h->n_partials);
+  g.total = g.off_dev + align256(sizeof(double) * (size_t)(m + 1));
+  return g;
+}
+
+// z = B v, one V-cycle: FP32 through the finest-level buffers, or FP64.
+sipg_status gmres_precond(sipg_handle* h, const double* v, double* z, cudaStream_t s) {
+  const size_t n = h->lv[h->L].ndofs;
+  if (h->prm.vcycle_precision == SIPG_FP32) {
+    float* bL = reinterpret_cast<float*>(h->ws + h->off_bL);
+    float* xL = reinterpret_cast<float*>(h->ws + h->off_xL);
+    SIPG_CHECK(convert_d2f(v, bL, n, s), "convert");
+    h->launches += 1;
+    sipg_status st = vcycle_T<float>(h, bL, xL, s);
+    if (st) return st;
+    SIPG_CHECK(convert_f2d(xL, z, n, s), "convert");
+    h->launches += 1;
+    return SIPG_OK;
+  }
+  return vcycle_T<double>(h, v, z, s);
+}
+
+struct GmresVectors {
+  sipg_handle* h;
+  cudaStream_t s;
+  long long n, ld;  // vector length, distance between consecutive vectors
+  double* V;
+  double* Z;
+  double* part;
+  double* dev;
+  double* v(int j) const { return V + (long long)j * ld; }
+  double* z(int j) const { return Z + (long long)j * ld; }
+  // out[i] = <Vb + i ld, w> for i < cnt, copied to the host
+  sipg_status dots(const double* Vb, int cnt, const double* w, double* out) {
+    SIPG_CHECK(gmres_mdot(h, Vb, ld, cnt, w, n, part, dev, s), "dot");
+    SIPG_CHECK(cudaMemcpyAsync(out, dev, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s), "D2H");
+    SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+    return SIPG_OK;
+  }
+  // V_0 = b - A x, *beta = ||V_0||_2
+  sipg_status residual(const double* b, const double* x, double* beta) {
+    SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_RESIDUAL, b, x, V, s), "residual");
+    h->launches += 1;
+    double rr = 0.0;
+    sipg_status st = dots(V, 1, V, &rr);
+    if (st) return st;
+    *beta = sqrt(rr);
+    return SIPG_OK;
+  }
+};
+
+sipg_status gmres_run(sipg_handle* h, const double* b, double* x, double rtol, int maxit, int m, char* work,
+                      sipg_info* info, cudaStream_t s) {
+  const GmresLayout lay = gmres_layout(h, m);
+  GmresVectors g{h, s, (long long)h->lv[h->L].ndofs, (long long)(lay.vec / sizeof(double)),
+                 reinterpret_cast<double*>(work), reinterpret_cast<double*>(work + lay.off_z),
+                 reinterpret_cast<double*>(work + lay.off_part), reinterpret_cast<double*>(work + lay.off_dev)};
+  double bb = 0.0, beta = 0.0;
+  sipg_status st = g.dots(b, 1, b, &bb);
+  if (st) return st;
+  const double bnorm = sqrt(bb);
+  st = g.residual(b, x, &beta);
+  if (st) return st;
+  std::vector<double> hist{beta};
+  sipg_status result = (isfinite(bnorm) && isfinite(beta)) ? SIPG_OK : SIPG_EBREAKDOWN;
+  bool conv = !(bnorm > 0.0) || beta <= rtol * bnorm;
+  int steps = 0;
+  // Hessenberg matrix (row-major, (m+1) x m), rotations, right-hand side
+  std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), y(m), hc(m + 1), tmp(m + 1);
+  auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  while (!conv && result == SIPG_OK && steps < maxit) {
+    const int mc = std::min(m, maxit - steps);
+    SIPG_CHECK(gmres_scale(h, g.v(0), 1.0 / beta, g.n, s), "scale");
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;  // completed steps of this cycle
+    while (j < mc) {
+      st = gmres_precond(h, g.v(j), g.z(j), s);
+      if (st) return st;
+      SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, g.z(j), g.v(j + 1), s), "apply");
+      h->launches += 1;
+      // classical Gram-Schmidt, applied twice: w -= sum_i <V_i, w> V_i
+      std::fill(hc.begin(), hc.end(), 0.0);
+      for (int pass = 0; pass < 2; ++pass) {
+        SIPG_CHECK(gmres_mdot(h, g.V, g.ld, j + 1, g.v(j + 1), g.n, g.part, g.dev, s), "dot");
+        SIPG_CHECK(gmres_maxpy(h, g.v(j + 1), g.V, g.ld, j + 1, g.dev, nullptr, -1.0, g.n, s), "axpy");
+        SIPG_CHECK(cudaMemcpyAsync(tmp.data(), g.dev, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s),
+                   "D2H");
+        SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+        for (int i = 0; i <= j; ++i) hc[i] += tmp[i];
+      }
+      double ww = 0.0;
+      st = g.dots(g.v(j + 1), 1, g.v(j + 1), &ww);
+      if (st) return st;
+      const double hn = sqrt(ww);
+      bool finite = isfinite(hn);
+      for (int i = 0; i <= j; ++i) finite = finite && isfinite(hc[i]);
+      if (!finite) {
+        result = SIPG_EBREAKDOWN;
+        break;
+      }
+      for (int i = 0; i <= j; ++i) Hat(i, j) = hc[i];
+      Hat(j + 1, j) = hn;
+      if (hn > 0.0) SIPG_CHECK(gmres_scale(h, g.v(j + 1), 1.0 / hn, g.n, s), "scale");
+      for (int i = 0; i < j; ++i) {  // rotations of the earlier steps
+        const double a = Hat(i, j), c = Hat(i + 1, j);
+        Hat(i, j) = cs[i] * a + sn[i] * c;
+        Hat(i + 1, j) = -sn[i] * a + cs[i] * c;
+      }
+      const double den = hypot(Hat(j, j), Hat(j + 1, j));
+      if (!(den > 0.0)) {
+        result = SIPG_EBREAKDOWN;
+        break;
+      }
+      cs[j] = Hat(j, j) / den;
+      sn[j] = Hat(j + 1, j) / den;
+      Hat(j, j) = den;
+      Hat(j + 1, j) = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++j;
+      ++steps;
+      hist.push_back(fabs(gv[j]));
+      if (fabs(gv[j]) <= rtol * bnorm || hn == 0.0) break;  // converged, or exact
+    }
+    if (j == 0) break;
+    // y = R^{-1} g (back substitution), x += Z y, true residual
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int q = i + 1; q < j; ++q) acc -= Hat(i, q) * y[q];
+      y[i] = acc / Hat(i, i);
+    }
+    SIPG_CHECK(gmres_maxpy(h, x, g.Z, g.ld, j, nullptr, y.data(), 1.0, g.n, s), "update");
+    st = g.residual(b, x, &beta);
+    if (st) return st;
+    hist.back() = beta;  // the true residual ends every cycle
+    if (!isfinite(beta)) result = SIPG_EBREAKDOWN;
+    conv = beta <= rtol * bnorm;
+  }
+  if (result == SIPG_OK && !conv) result = SIPG_ENOCONV;
+  {
+    // a bounded grid-barrier wait that ran out (fused smoothing steps)
+    int status = 0;
+    SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_sync + 2 * sizeof(unsigned int), sizeof(int),
+                               cudaMemcpyDeviceToHost, s),
+               "status D2H");
+    SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+    if (status != 0) {
+      SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+      result = SIPG_ETIMEOUT;
+    }
+  }
+  if (info) {
+    info->iterations = steps;
+    info->status = result;
+    info->rel_residual = bnorm > 0.0 ? beta / bnorm : 0.0;
+    double nu = 0.0;
+    if (hist.size() > 1 && hist.front() > 0.0) {
+      double rbar = pow(hist.back() / hist.front(), 1.0 / (double)(hist.size() - 1));
+      nu = (rbar > 0.0 && rbar < 1.0) ? -8.0 / log10(rbar) : INFINITY;
+    }
+    info->nu = nu;
+    int cnt = 0;
+    if (info->history && info->history_capacity > 0) {
+      cnt = std::min((int)hist.size(), info->history_capacity);
+      for (int i = 0; i < cnt; ++i) info->history[i] = hist[i];
+    }
+    info->history_len = cnt;
+  }
+  if (result == SIPG_ETIMEOUT) h->err = "a bounded grid-barrier wait in the smoother timed out";
+  if (result == SIPG_ENOCONV) h->err = "GMRES reached maxit before rtol";
+  if (result == SIPG_EBREAKDOWN) h->err = "GMRES breakdown (non-finite scalar)";
+  return result;
+}
+
 // Autotuning of the smoothing step, per level: time each candidate launch
 // path (colour by colour with the default or the half interior tile, or one
 // fused launch where that applies) on the level's workspace vectors (zeroed;
@@ -766,6 +956,25 @@ sipg_status sipg_solve(sipg_handle* h, const double* b, double* x, double rtol, 
   if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
   if (!(rtol > 0.0) || maxit < 0) return fail(h, SIPG_EINVAL, "bad rtol or maxit");
   return fcg_solve(h, b, x, rtol, maxit, info, S(stream));
+}
+
+size_t sipg_gmres_workspace_bytes(const sipg_handle* h, int restart) {
+  if (!h || restart < 1 || restart > SIPG_GMRES_MAX_RESTART) return 0;
+  return gmres_layout(h, restart).total;
+}
+
+sipg_status sipg_gmres_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit, int restart,
+                             void* work, size_t work_bytes, sipg_info* info, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (h->prm.nrhs != 1) return fail(h, SIPG_EUNSUPPORTED, "GMRES solves one right-hand side (nrhs = 1)");
+  if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  if (!(rtol > 0.0) || maxit < 0) return fail(h, SIPG_EINVAL, "bad rtol or maxit");
+  if (restart < 1 || restart > SIPG_GMRES_MAX_RESTART) return fail(h, SIPG_EINVAL, "restart out of range");
+  if (!work || (reinterpret_cast<uintptr_t>(work) & 255) != 0)
+    return fail(h, SIPG_EINVAL, "GMRES workspace must be 256-byte aligned");
+  if (work_bytes < gmres_layout(h, restart).total) return fail(h, SIPG_EINVAL, "GMRES workspace too small");
+  return gmres_run(h, b, x, rtol, maxit, restart, static_cast<char*>(work), info, S(stream));
 }
 
 sipg_status sipg_adjoint_solve(sipg_handle* h, const double* g, double* lambda, double rtol, int maxit,

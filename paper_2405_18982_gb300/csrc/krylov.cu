@@ -7,6 +7,8 @@
 // V-cycle output fused with <r, z> and <z, q>).  Mixed precision: Sec. 5.2.
 #include <math.h>
 
+#include <algorithm>
+
 #include "sipg_internal.cuh"
 
 namespace {
@@ -207,9 +209,78 @@ __global__ void f2d_kernel(const float* a, double* b, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (double)a[i];
 }
 
+// ---------------------------------------------------------------- GMRES
+// partial <V_i, w> of vector i = blockIdx.y (V_i starts at V + i * ld)
+__global__ void __launch_bounds__(RB) mdot_partial_kernel(const double* V, long long ld, const double* w,
+                                                          long long n, double* partials) {
+  const double* v = V + (long long)blockIdx.y * ld;
+  double acc[1] = {0.0};
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) acc[0] = fma(v[i], w[i], acc[0]);
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
+}
+
+// out[i] = the nb partials of vector i = blockIdx.x summed in a fixed order
+__global__ void __launch_bounds__(RB) mdot_finalize_kernel(const double* partials, int nb, double* out) {
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < nb; i += RB) acc[0] += partials[(long long)blockIdx.x * nb + i];
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc[0];
+}
+
+struct GmresCoef {
+  double c[SIPG_GMRES_MAXM + 1];
+};
+
+// w += sign * sum_{q < cnt} c_q V_q with c from device memory (cdev) or from
+// the parameter block (cdev == nullptr)
+__global__ void __launch_bounds__(RB) maxpy_kernel(double* w, const double* V, long long ld, int cnt,
+                                                   const double* cdev, GmresCoef cpar, double sign, long long n) {
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+    double acc = 0.0;
+    for (int q = 0; q < cnt; ++q) acc = fma(cdev ? cdev[q] : cpar.c[q], V[q * ld + i], acc);
+    w[i] = fma(sign, acc, w[i]);
+  }
+}
+
+__global__ void __launch_bounds__(RB) scale_kernel(double* w, double a, long long n) {
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) w[i] *= a;
+}
+
 }  // namespace
 
 static inline long long fine_n(const sipg_handle* h) { return (long long)h->lv[h->L].ndofs; }
+
+cudaError_t gmres_mdot(sipg_handle* h, const double* V, long long ld, int cnt, const double* w, long long n,
+                       double* partials, double* out, cudaStream_t s) {
+  if (cnt < 1 || cnt > SIPG_GMRES_MAXM + 1) return cudaErrorInvalidValue;
+  dim3 grid(h->n_partials, cnt);
+  mdot_partial_kernel<<<grid, RB, 0, s>>>(V, ld, w, n, partials);
+  mdot_finalize_kernel<<<cnt, RB, 0, s>>>(partials, h->n_partials, out);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_maxpy(sipg_handle* h, double* w, const double* V, long long ld, int cnt, const double* cdev,
+                        const double* chost, double sign, long long n, cudaStream_t s) {
+  if (cnt < 1 || cnt > SIPG_GMRES_MAXM + 1 || (!cdev && !chost)) return cudaErrorInvalidValue;
+  GmresCoef cp;
+  for (int q = 0; q <= SIPG_GMRES_MAXM; ++q) cp.c[q] = (!cdev && q < cnt) ? chost[q] : 0.0;
+  const int blocks = std::min(ceil_div(n, RB), 64 * h->num_sms);
+  maxpy_kernel<<<blocks, RB, 0, s>>>(w, V, ld, cnt, cdev, cp, sign, n);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_scale(sipg_handle* h, double* w, double a, long long n, cudaStream_t s) {
+  const int blocks = std::min(ceil_div(n, RB), 64 * h->num_sms);
+  scale_kernel<<<blocks, RB, 0, s>>>(w, a, n);
+  h->launches += 1;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dot(sipg_handle* h, const double* a, const double* b, double* out,
                        cudaStream_t s) {

@@ -12,6 +12,7 @@
 #define SIPG_MAXP 16   // 1D patch size 2n
 #define SIPG_MAXPE 18  // 2n plus one halo node on each side
 #define SIPG_MAXM0 64  // 1D size of the coarsest level, N_0 * n
+#define SIPG_GMRES_MAXM SIPG_GMRES_MAX_RESTART
 
 // Per-level constants, written by the device setup kernel (FP64) and copied
 // to an FP32 twin.  All 1D operators include kappa; physical cell size h.
@@ -193,6 +194,16 @@ cudaError_t krylov_after_precond(sipg_handle* h, int first, const double* r, con
                                  int zsrc_is_float, cudaStream_t s);
 cudaError_t krylov_after_apply(sipg_handle* h, cudaStream_t s);
 cudaError_t krylov_update_xr(sipg_handle* h, double* x, void* bL, int bL_is_float, cudaStream_t s);
+// GMRES vector kernels (krylov.cu); nrhs = 1.  out[i] = <V_i, w> for
+// i < cnt (V_i = V + i * ld), deterministic two-stage sums (partials holds
+// cnt * n_partials doubles); w += sign * sum_q c_q V_q with c in device
+// memory (cdev) or copied from the host into the launch parameters (chost);
+// w *= a.
+cudaError_t gmres_mdot(sipg_handle* h, const double* V, long long ld, int cnt, const double* w, long long n,
+                       double* partials, double* out, cudaStream_t s);
+cudaError_t gmres_maxpy(sipg_handle* h, double* w, const double* V, long long ld, int cnt, const double* cdev,
+                        const double* chost, double sign, long long n, cudaStream_t s);
+cudaError_t gmres_scale(sipg_handle* h, double* w, double a, long long n, cudaStream_t s);
 cudaError_t convert_d2f(const double* a, float* b, size_t n, cudaStream_t s);
 cudaError_t convert_f2d(const float* a, double* b, size_t n, cudaStream_t s);
 cudaError_t copy_or_zero(void* dst, size_t bytes, cudaStream_t s);

@@ -61,6 +61,14 @@ def test_host_only_calls_without_gpu(lib):
     # calls before binding a workspace are rejected, not crashed
     assert lib.sipg_apply(h, 0, 0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == -8
     assert b"workspace" in lib.sipg_last_error(h)
+    # GMRES: restart bounds, workspace >= 2 restart + 1 finest-level vectors,
+    # and no solve before binding
+    nf = 64 ** 3 * 64
+    assert lib.sipg_gmres_workspace_bytes(h, 0) == 0 and lib.sipg_gmres_workspace_bytes(h, 65) == 0
+    assert lib.sipg_gmres_workspace_bytes(h, 1) >= 3 * nf * 8
+    assert lib.sipg_gmres_workspace_bytes(h, 64) >= 129 * nf * 8
+    assert lib.sipg_gmres_solve(h, ctypes.c_void_p(16), ctypes.c_void_p(32), 1e-8, 10, 4,
+                                ctypes.c_void_p(256), 1 << 40, None, None) == -8
     lib.sipg_destroy(h)
     assert lib.sipg_version().startswith(b"sipg")
 
