@@ -25,6 +25,11 @@ Readings of the paper (where it is silent or ambiguous):
     and that ignoring it makes the residual inconsistent; keeping its
     patch-side half instead gives iteration counts that grow with the level,
     unlike Table 2;
+  * the paper's full kernel ("full", Sec. 3.1, Table 1): V_j is every DoF of
+    the 2^d patch cells and A_j the principal block of A on them; the residual
+    is updated globally once per colour (r = b - A x), and every patch of the
+    colour adds A_j^{-1} R_j r.  Same-colour patches share faces but no DoFs,
+    so inside a colour the corrections are additive;
   * colours: c = sum_e (v_e mod 2) 2^e for vertex index v; pre-smoothing visits
     colours 0..2^d-1, post-smoothing visits them in reverse;
   * outer solver: flexible CG with beta = <z_{i+1}, r_{i+1} - r_i> / <z_i, r_i>,
@@ -129,10 +134,12 @@ class Level:
             full = element_blocks(dim, k, N, kappa, eta)
             no_last = element_blocks(dim, k, N, kappa, eta, part="no_last")
         for p in self.patches:
+            if variant == "full":
+                p["V"] = p["dofs"]                   # every DoF of the patch cells
             V = p["V"]
             Aj = self.A[V][:, V].toarray()           # A_j = R_j A R_j^T
             p["chol"] = sla.cho_factor(Aj, lower=True)
-            if variant == "consistent":
+            if variant in ("consistent", "full"):
                 p["rows"] = self.A[V]                # all columns: R_j A
                 p["cols"] = None
             elif variant == "paper":
@@ -162,7 +169,8 @@ def smooth(level, x, b, reverse=False, patch_order=None, colours=None):
     S_l(x, b) (Algorithm 1): colours in sequence; inside a colour, patches
     one after another (the paper's parallel loop; the tests check that the
     order inside a colour does not change the result), each doing
-    r_j <- local residual; x <- x + R_j^T A_j^{-1} r_j.
+    r_j <- local residual; x <- x + R_j^T A_j^{-1} r_j (for the full kernel
+    the residual of the whole colour is computed once before its patches).
     ``colours`` restricts the sweep to the listed colours (in that order)."""
     x = np.array(x, dtype=np.float64, copy=True)
     order = level.colour_order(reverse) if colours is None else list(colours)
@@ -170,6 +178,12 @@ def smooth(level, x, b, reverse=False, patch_order=None, colours=None):
         members = [p for p in level.patches if p["colour"] == c]
         if patch_order is not None:
             members = [members[i] for i in patch_order(c, len(members))]
+        if level.variant == "full":
+            # full kernel: one global residual per colour, additive inside it
+            r = b - level.A @ x
+            for p in members:
+                x[p["V"]] += sla.cho_solve(p["chol"], r[p["V"]])
+            continue
         for p in members:
             r = local_residual(p, b, x)
             x[p["V"]] += sla.cho_solve(p["chol"], r)

@@ -376,3 +376,106 @@ def test_gmres_dirichlet_kernel_reproduces_table2():
         printed = ref[L - 2, k - 2]
         assert abs(got[(k, L)] - printed) <= 0.2 * printed, (k, L, got[(k, L)], printed)
     assert got[(3, 3)] <= 1.2 * got[(3, 2)]
+
+
+# ---------------------------------------------------------------- full kernel
+@pytest.mark.parametrize("dim,k", [(2, 2), (2, 3), (3, 2)])
+def test_full_kernel_is_exact_on_a_one_patch_mesh(dim, k):
+    # N = 2: one interior vertex whose patch is the whole mesh, so the full
+    # kernel's local space is everything and one smoothing step solves Ax = b
+    lev = Level(dim, k, 2, variant="full")
+    assert len(lev.patches) == 1 and len(lev.patches[0]["V"]) == lev.ndof
+    b = np.random.default_rng(3).standard_normal(lev.ndof)
+    x = smooth(lev, np.zeros(lev.ndof), b)
+    assert np.allclose(x, np.linalg.solve(lev.A.toarray(), b), rtol=0, atol=1e-11 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("dim,k,N", [(2, 3, 4), (3, 2, 4)])
+def test_full_kernel_patch_matrix_is_a_kronecker_sum(dim, k, N):
+    # A_j over all 2n nodes per direction = sum_d (x) (L_patch in d, M_patch
+    # elsewhere) with L_patch, M_patch the global 1D matrices restricted to
+    # the patch's 2n nodes (Sec. 2.2 on the patch), and its fast
+    # diagonalisation (Eq. fast_inverse) inverts it
+    lev = Level(dim, k, N, variant="full")
+    L1, M1 = one_d_matrices(k, N)
+    n = k + 1
+    for p in lev.patches[:: max(1, len(lev.patches) // 4)]:
+        v = p["vertex"]
+        mats = []
+        for e in range(dim):
+            idx = np.arange((v[e] - 1) * n, (v[e] + 1) * n)
+            mats.append((L1[np.ix_(idx, idx)], M1[np.ix_(idx, idx)]))
+        # patch-local lexicographic order (direction 0 fastest) -> global
+        loc = np.zeros((2 * n,) * dim, dtype=np.int64)
+        for a in np.ndindex(*(2 * n,) * dim):
+            cell = [v[e] - 1 + a[e] // n for e in range(dim)]
+            node = [a[e] % n for e in range(dim)]
+            cf = sum(cell[e] * N ** e for e in range(dim))
+            nf = sum(node[e] * n ** e for e in range(dim))
+            loc[a] = cf * n ** dim + nf
+        order = loc.transpose(*range(dim)[::-1]).ravel()     # direction 0 fastest
+        Aj = lev.A[order][:, order].toarray()
+        K = np.zeros_like(Aj)
+        for d in range(dim):
+            term = np.ones((1, 1))
+            for e in range(dim - 1, -1, -1):
+                term = np.kron(term, mats[e][0] if e == d else mats[e][1])
+            K += term
+        assert np.abs(Aj - K).max() <= 1e-12 * np.abs(Aj).max()
+        lam_S = [sla.eigh(Le, Me) for Le, Me in mats]
+        lam = sum(np.meshgrid(*[ls[0] for ls in lam_S[::-1]], indexing="ij")[::-1][d] for d in range(dim))
+        S = np.ones((1, 1))
+        for e in range(dim - 1, -1, -1):
+            S = np.kron(S, lam_S[e][1])
+        inv = S @ np.diag(1.0 / lam.ravel()) @ S.T
+        assert np.abs(inv @ Aj - np.eye(len(Aj))).max() < 1e-9
+
+
+def test_gmres_full_kernel_near_table1():
+    # Table 1 (full kernel) against Table 2 (Dirichlet kernel): the full kernel
+    # needs fewer iterations, and nu does not grow with L.  The oracle's nu
+    # lies 25-40 % below the printed values (Q3: 2.25 / 2.34 at L = 2 / 3
+    # against 3.4 / 3.7), so the table itself is matched to a factor 1.6 only.
+    from oracle.assembly import rhs_from_nodal
+    from oracle.mg import gmres
+    ref1 = np.loadtxt(os.path.join(GOLDEN, "table1_full_nu.txt"))
+    got = {}
+    for L in (2, 3):
+        N = 1 << L
+        nu = {}
+        for variant in ("full", "paper"):
+            H = Hierarchy(3, 3, N, L, variant=variant)
+            b = rhs_from_nodal(3, 3, N, np.ones(H.A.shape[0]))
+            _, hist = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=60)
+            nu[variant] = fractional_iterations(hist)
+        printed = ref1[L - 2, 1]
+        assert printed / 1.6 <= nu["full"] <= printed * 1.6, (L, nu, printed)
+        assert nu["full"] < nu["paper"]
+        got[L] = nu["full"]
+    assert got[3] <= 1.2 * got[2]
+
+
+@pytest.mark.parametrize("dim,k,N", [(2, 2, 4), (2, 3, 8), (3, 1, 4)])
+def test_full_kernel_colour_pass_is_block_jacobi(dim, k, N):
+    # the residual is updated once per colour ("globally", Sec. 3.1), so one
+    # colour pass is a block-Jacobi step over the colour's patches: solve
+    # with A on the union of their DoFs after deleting the couplings between
+    # different patches (they share faces, not DoFs), add, leave the rest
+    lev = Level(dim, k, N, variant="full")
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(lev.ndof)
+    x0 = rng.standard_normal(lev.ndof)
+    A = lev.A.toarray()
+    r = b - A @ x0
+    for c in range(2 ** dim):
+        owner = -np.ones(lev.ndof, dtype=np.int64)
+        for i, p in enumerate(lev.patches):
+            if p["colour"] == c:
+                assert np.all(owner[p["V"]] < 0)
+                owner[p["V"]] = i
+        U = np.flatnonzero(owner >= 0)
+        D = A[np.ix_(U, U)] * (owner[U][:, None] == owner[U][None, :])
+        expect = x0.copy()
+        expect[U] += np.linalg.solve(D, r[U])
+        got = smooth(lev, x0, b, colours=[c])
+        assert np.allclose(got, expect, rtol=0, atol=1e-10 * np.abs(expect).max())
