@@ -579,7 +579,8 @@ def run_table2(args):
     the coarsest level, GMRES to 1e-8 preconditioned from the right by one
     V-cycle whose smoother uses the Dirichlet-kernel residual; nu (Sec. 3.3),
     steps and time to solution with the FP64 and the FP32 V-cycle, the
-    consistent residual beside it, and the value printed in Table 2.  Cases
+    consistent residual and the full kernel (Table 1's setting) beside it,
+    and the values printed in Tables 2 and 1.  Cases
     k = 3..7, L = 2..7 up to --max-dofs DoFs.  One JSON line per case."""
     import time
 
@@ -587,9 +588,10 @@ def run_table2(args):
     import torch
     import paper_2405_18982_gb300 as pkg
     from paper_2405_18982_gb300 import (SIPG, SIPG_FP32, SIPG_FP64, SIPG_SMOOTHER_CONSISTENT,
-                                        SIPG_SMOOTHER_PAPER, Params)
+                                        SIPG_SMOOTHER_FULL, SIPG_SMOOTHER_PAPER, Params)
     pkg.load(pkg.build())
     printed = np.loadtxt(os.path.join(ROOT, "tests", "golden", "table2_dirichlet_nu.txt"))
+    printed1 = np.loadtxt(os.path.join(ROOT, "tests", "golden", "table1_full_nu.txt"))
     for L in range(2, 8):
         for k in range(3, 8):
             n = (1 << L) ** 3 * (k + 1) ** 3
@@ -597,8 +599,10 @@ def run_table2(args):
                 continue
             row = {"mode": "table2", "degree": k, "L": L, "dofs": n,
                    "nu_table2": None if np.isnan(printed[L - 2, k - 2]) else float(printed[L - 2, k - 2])}
+            row["nu_table1"] = None if np.isnan(printed1[L - 2, k - 2]) else float(printed1[L - 2, k - 2])
             for tag, prec, sm in (("fp64", SIPG_FP64, SIPG_SMOOTHER_PAPER), ("mixed", SIPG_FP32, SIPG_SMOOTHER_PAPER),
-                                  ("consistent_mixed", SIPG_FP32, SIPG_SMOOTHER_CONSISTENT)):
+                                  ("consistent_mixed", SIPG_FP32, SIPG_SMOOTHER_CONSISTENT),
+                                  ("full_mixed", SIPG_FP32, SIPG_SMOOTHER_FULL)):
                 s = SIPG(Params(dim=3, degree=k, log2_cells=L, n_levels=L, vcycle_precision=prec, smoother=sm))
                 f = torch.ones(1, s.ndofs(), dtype=torch.float64, device="cuda")
                 b = torch.zeros_like(f)

@@ -82,7 +82,15 @@ typedef enum {
    * Dirichlet kernel, inconsistent residual): Abar_j is the form on the
    * patch cells in which the last face term -[[u]].{grad v} of the
    * patch-boundary faces inside the domain is left out (Sec. 3.1). */
-  SIPG_SMOOTHER_PAPER = 1
+  SIPG_SMOOTHER_PAPER = 1,
+  /* The paper's full kernel (Sec. 3.1, Table 1): V_j is every DoF of the
+   * 2^d patch cells and A_j the principal block of A on them, inverted by
+   * fast diagonalisation with the 1D eigenpairs of the whole 2n-node patch.
+   * The residual b - A x is updated globally once per colour (the choice
+   * Sec. 3.1 makes for this kernel), then every patch of the colour adds its
+   * correction: same-colour patches share faces but no DoFs, so inside a
+   * colour the corrections are additive. */
+  SIPG_SMOOTHER_FULL = 2
 } sipg_smoother;
 
 typedef struct {

@@ -133,11 +133,25 @@ class Level:
         if variant == "paper":
             full = element_blocks(dim, k, N, kappa, eta)
             no_last = element_blocks(dim, k, N, kappa, eta, part="no_last")
+        factors = {}
         for p in self.patches:
             if variant == "full":
                 p["V"] = p["dofs"]                   # every DoF of the patch cells
             V = p["V"]
             Aj = self.A[V][:, V].toarray()           # A_j = R_j A R_j^T
+            if variant == "full":
+                # patches of one type have equal A_j on the uniform mesh: the
+                # (large) factor is kept once per type, after checking that
+                p["rows"], p["cols"] = self.A[V], None
+                if p["type"] in factors:
+                    A0, f0 = factors[p["type"]]
+                    if np.abs(Aj - A0).max() > 1e-13 * np.abs(A0).max():
+                        raise AssertionError("patches of one type differ")
+                    p["chol"] = f0
+                else:
+                    p["chol"] = sla.cho_factor(Aj, lower=True)
+                    factors[p["type"]] = (Aj, p["chol"])
+                continue
             p["chol"] = sla.cho_factor(Aj, lower=True)
             if variant in ("consistent", "full"):
                 p["rows"] = self.A[V]                # all columns: R_j A

@@ -662,7 +662,9 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   if (!(p->kappa > 0.0) || !isfinite(p->kappa)) return SIPG_EINVAL;
   if (!(p->penalty_factor > 0.0) || !isfinite(p->penalty_factor)) return SIPG_EINVAL;
   if (p->vcycle_precision != SIPG_FP64 && p->vcycle_precision != SIPG_FP32) return SIPG_EINVAL;
-  if (p->smoother != SIPG_SMOOTHER_CONSISTENT && p->smoother != SIPG_SMOOTHER_PAPER) return SIPG_EINVAL;
+  if (p->smoother != SIPG_SMOOTHER_CONSISTENT && p->smoother != SIPG_SMOOTHER_PAPER &&
+      p->smoother != SIPG_SMOOTHER_FULL)
+    return SIPG_EINVAL;
   if (p->nrhs < 1 || p->nrhs > 65535) return SIPG_EINVAL;
   const int n = p->degree + 1;
   const int L = p->n_levels - 1;
@@ -810,7 +812,7 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
   SIPG_CHECK(cudaMemcpyAsync(h->hc32.data(), h->c32(0), sizeof(LevelConst<float>) * nl, cudaMemcpyDeviceToHost, s),
              "constants D2H");
   SIPG_CHECK(cudaStreamSynchronize(s), "setup sync");
-  if (h->autotune) {
+  if (h->autotune && h->prm.smoother != SIPG_SMOOTHER_FULL) {  // the full kernel has one launch path
     const sipg_status st = h->prm.vcycle_precision == SIPG_FP32 ? tune_T<float>(h, s) : tune_T<double>(h, s);
     if (st) return st;
   }

@@ -386,6 +386,18 @@ __global__ void setup_levels_kernel(LevelConst<double>* out, int k, int N_finest
       c.lam[t][r] = (r < p) ? lam[r] : 0.0;
       for (int s = 0; s < SIPG_MAXP; ++s) c.S[t][r][s] = (r < p && s < p) ? Ss[r * SIPG_MAXP + s] : 0.0;
     }
+    // full kernel: the same eigenproblem on all P patch nodes
+    for (int r = 0; r < P; ++r)
+      for (int s = 0; s < P; ++s) {
+        As[r * SIPG_MAXP + s] = Lp[r][s];
+        Bs[r * SIPG_MAXP + s] = Mp[r][s];
+      }
+    ok = generalised_eigen(P, As, Bs, SIPG_MAXP, Ss, lam, W1, W2);
+    if (!ok) atomicExch(status, 1);
+    for (int r = 0; r < SIPG_MAXP; ++r) {
+      c.lamf[t][r] = (r < P) ? lam[r] : 0.0;
+      for (int s = 0; s < SIPG_MAXP; ++s) c.Sf[t][r][s] = (r < P && s < P) ? Ss[r * SIPG_MAXP + s] : 0.0;
+    }
   } else if (t == 4 && l == 0) {
     // coarsest level: global 1D SIPG matrix and mass, N n x N n
     const int m = N * n;
@@ -462,6 +474,8 @@ __global__ void constants_to_float_kernel(const LevelConst<double>* in, LevelCon
   SIPG_CONVERT(Mr)
   SIPG_CONVERT(S)
   SIPG_CONVERT(lam)
+  SIPG_CONVERT(Sf)
+  SIPG_CONVERT(lamf)
   SIPG_CONVERT(Pc)
   SIPG_CONVERT(nodes)
   SIPG_CONVERT(S0)

@@ -51,6 +51,10 @@ struct LevelConst {
   T Mr[4][SIPG_MAXP][SIPG_MAXPE];
   T S[4][SIPG_MAXP][SIPG_MAXP];  // M-orthonormal generalised eigenvectors (columns)
   T lam[4][SIPG_MAXP];
+  // Full-kernel patch (all 2n nodes) of type t: eigenpairs of the 1D patch
+  // matrices Lp S = Mp S Lambda, S M-orthonormal (columns).
+  T Sf[4][SIPG_MAXP][SIPG_MAXP];
+  T lamf[4][SIPG_MAXP];
   // Canonical embedding: Pc[o][i][j] = phi_j((o + xi_i) / 2).
   T Pc[2][SIPG_MAXN][SIPG_MAXN];
   T nodes[SIPG_MAXN];  // Gauss-Lobatto nodes on [0,1]
@@ -164,6 +168,12 @@ cudaError_t launch_manufactured(const sipg_handle* h, double* f, cudaStream_t s)
 template <typename T>
 cudaError_t launch_smooth_colour(const sipg_handle* h, int level, int colour, const T* b, T* x,
                                  cudaStream_t s);
+// Full-kernel colour pass (smooth_full.cu): r = b - A x on the whole level
+// into the level's residual buffer, then every patch of the colour adds
+// A_j^{-1} R_j r.  Reports its launches.
+template <typename T>
+cudaError_t launch_full_colour(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s,
+                               int* launches);
 // One smoothing step (all colours, reversed order if `reverse`); reports the
 // number of kernels it launched.
 template <typename T>

@@ -42,6 +42,10 @@ cudaError_t step_dim(const sipg_handle* h, int level, int reverse, const T* b, T
 template <typename T>
 cudaError_t launch_smooth_colour(const sipg_handle* h, int level, int colour, const T* b, T* x,
                                  cudaStream_t s) {
+  if (h->prm.smoother == SIPG_SMOOTHER_FULL) {
+    int nl = 0;
+    return launch_full_colour<T>(h, level, colour, b, x, s, &nl);
+  }
   return h->prm.dim == 2 ? colour_dim<2, T>(h, level, colour, b, x, s) : colour_dim<3, T>(h, level, colour, b, x, s);
 }
 template cudaError_t launch_smooth_colour<double>(const sipg_handle*, int, int, const double*, double*,
@@ -52,6 +56,17 @@ template cudaError_t launch_smooth_colour<float>(const sipg_handle*, int, int, c
 template <typename T>
 cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s,
                                int* launches) {
+  const int nc = 1 << h->prm.dim;
+  if (h->prm.smoother == SIPG_SMOOTHER_FULL) {
+    *launches = 0;
+    for (int i = 0; i < nc; ++i) {
+      int nl = 0;
+      cudaError_t e = launch_full_colour<T>(h, level, reverse ? nc - 1 - i : i, b, x, s, &nl);
+      *launches += nl;
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (h->fuse_small_levels && h->tuned_path(sizeof(T) == 4 ? 1 : 0, level) != 1) {
     cudaError_t e = h->prm.dim == 2 ? step_dim<2, T>(h, level, reverse, b, x, s)
                                     : step_dim<3, T>(h, level, reverse, b, x, s);
@@ -61,7 +76,6 @@ cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, con
     }
     if (e != cudaErrorNotSupported) return e;
   }
-  const int nc = 1 << h->prm.dim;
   *launches = 0;
   for (int i = 0; i < nc; ++i) {
     const int c = reverse ? nc - 1 - i : i;

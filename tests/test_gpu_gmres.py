@@ -34,7 +34,7 @@ def hierarchy(dim, k, N, nl, kappa=1.0, variant="consistent"):
     return _HIER[key]
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["consistent", "paper"])
+@pytest.mark.parametrize("variant", [0, 1, 2], ids=["consistent", "paper", "full"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_gmres_history_matches_oracle(case, variant):
     # same V-cycle (FP64), same GMRES: the residual after every step agrees
@@ -44,7 +44,7 @@ def test_gmres_history_matches_oracle(case, variant):
     dim, k, l2, nl = case
     N = 1 << l2
     s = make(dim, k, l2, nl, kappa=1.1, smoother=variant)
-    H = hierarchy(dim, k, N, nl, kappa=1.1, variant="consistent" if variant == 0 else "paper")
+    H = hierarchy(dim, k, N, nl, kappa=1.1, variant=("consistent", "paper", "full")[variant])
     b = rhs_from_nodal(dim, k, N, inputs.normal(700, H.A.shape[0]))
     x_ref, h_ref = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-10, maxit=100, restart=30)
     xd = dev(np.zeros_like(b))
