@@ -25,6 +25,17 @@ Readings of the paper (where it is silent or ambiguous):
     and that ignoring it makes the residual inconsistent; keeping its
     patch-side half instead gives iteration counts that grow with the level,
     unlike Table 2;
+  * the paper's clamped kernel ("clamped", Sec. 3.1, Table 2 right): V_j is
+    the functions on the patch cells whose value and normal derivative vanish
+    on the patch boundary inside the domain (no condition at a patch end on
+    the domain boundary, as for the Dirichlet kernel), (2k-2)^d functions for
+    an interior patch.  The paper spans it by a Hermite-type basis; here it is
+    the same space written in the Lagrange basis (an orthonormal basis of the
+    null space of the end conditions per direction, tensorised), so the
+    correction x += B (B^T A_D B)^{-1} B^T R_D (b - A x) is the paper's, while
+    the Euclidean residual norm of the outer solver (and hence nu) is that of
+    the Lagrange basis.  All patch-boundary face terms vanish for these test
+    functions, so the residual needs only the patch cells and is exact;
   * the paper's full kernel ("full", Sec. 3.1, Table 1): V_j is every DoF of
     the 2^d patch cells and A_j the principal block of A on them; the residual
     is updated globally once per colour (r = b - A x), and every patch of the
@@ -42,7 +53,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from .assembly import assemble, element_blocks, principal_block
-from .basis import gauss_lobatto, lagrange_values, tensor_index
+from .basis import gauss_lobatto, lagrange_derivatives, lagrange_values, tensor_index
 from .layout import cell_multi_index, dof_index
 
 
@@ -78,6 +89,33 @@ def prolongation(dim, k, Nc):
 
 
 # ---------------------------------------------------------------- patches
+def clamped_basis_1d(k, lo_on_boundary, hi_on_boundary):
+    """(2n, m) orthonormal basis of the 1D clamped patch space in the Lagrange
+    coefficients of the two patch cells: the null space of the conditions
+    v = 0 and v' = 0 at each patch end that is not on the domain boundary
+    (Sec. 3.1, clamped kernel).  m = 2k - 2 for an interior patch."""
+    n = k + 1
+    nodes, _ = gauss_lobatto(k)
+    val0 = lagrange_values(nodes, np.array([0.0]))[0]
+    val1 = lagrange_values(nodes, np.array([1.0]))[0]
+    der0 = lagrange_derivatives(nodes, np.array([0.0]))[0]
+    der1 = lagrange_derivatives(nodes, np.array([1.0]))[0]
+    rows = []
+    if not lo_on_boundary:                      # low end of cell 0
+        for f in (val0, der0):
+            r = np.zeros(2 * n)
+            r[:n] = f
+            rows.append(r)
+    if not hi_on_boundary:                      # high end of cell 1
+        for f in (val1, der1):
+            r = np.zeros(2 * n)
+            r[n:] = f
+            rows.append(r)
+    if not rows:
+        return np.eye(2 * n)
+    return sla.null_space(np.array(rows))
+
+
 def vertex_patches(dim, k, N, variant="consistent"):
     """All vertex patches of the N^d mesh (one per interior vertex).
 
@@ -135,11 +173,17 @@ class Level:
             no_last = element_blocks(dim, k, N, kappa, eta, part="no_last")
         factors = {}
         for p in self.patches:
-            if variant == "full":
+            p["B"] = None
+            if variant in ("full", "clamped"):
                 p["V"] = p["dofs"]                   # every DoF of the patch cells
             V = p["V"]
             Aj = self.A[V][:, V].toarray()           # A_j = R_j A R_j^T
-            if variant == "full":
+            if variant == "clamped":
+                if k < 2:
+                    raise ValueError("the clamped kernel needs k >= 2")
+                p["B"] = self._clamped_basis(p)
+                Aj = p["B"].T @ Aj @ p["B"]          # A on the clamped space
+            if variant in ("full", "clamped"):
                 # patches of one type have equal A_j on the uniform mesh: the
                 # (large) factor is kept once per type, after checking that
                 p["rows"], p["cols"] = self.A[V], None
@@ -165,6 +209,24 @@ class Level:
             else:
                 raise ValueError(variant)
 
+    def _clamped_basis(self, p):
+        """Tensor product of the 1D clamped bases, rows in the order of
+        p["dofs"] (cell-wise lexicographic)."""
+        dim, k, N = self.dim, self.k, self.N
+        n = k + 1
+        v = p["vertex"]
+        B1 = [clamped_basis_1d(k, v[e] == 1, v[e] == N - 1) for e in range(dim)]
+        B = np.ones((1, 1))
+        for e in range(dim - 1, -1, -1):            # patch-lexicographic, direction 0 fastest
+            B = np.kron(B, B1[e])
+        out = np.zeros((len(p["dofs"]), B.shape[1]))
+        for row, t in enumerate(np.ndindex(*(2 * n,) * dim)):
+            a = t[::-1]                              # (a_0, a_1, ...), a_0 fastest
+            cell = sum((v[e] - 1 + a[e] // n) * N ** e for e in range(dim))
+            node = sum((a[e] % n) * n ** e for e in range(dim))
+            out[np.searchsorted(p["dofs"], cell * n ** dim + node)] = B[row]
+        return out
+
     def colour_order(self, reverse=False):
         order = list(range(2 ** self.dim))
         return order[::-1] if reverse else order
@@ -184,7 +246,9 @@ def smooth(level, x, b, reverse=False, patch_order=None, colours=None):
     one after another (the paper's parallel loop; the tests check that the
     order inside a colour does not change the result), each doing
     r_j <- local residual; x <- x + R_j^T A_j^{-1} r_j (for the full kernel
-    the residual of the whole colour is computed once before its patches).
+    the residual of the whole colour is computed once before its patches;
+    for the clamped kernel A_j and the correction live in the span of the
+    patch's clamped basis B).
     ``colours`` restricts the sweep to the listed colours (in that order)."""
     x = np.array(x, dtype=np.float64, copy=True)
     order = level.colour_order(reverse) if colours is None else list(colours)
@@ -200,7 +264,10 @@ def smooth(level, x, b, reverse=False, patch_order=None, colours=None):
             continue
         for p in members:
             r = local_residual(p, b, x)
-            x[p["V"]] += sla.cho_solve(p["chol"], r)
+            if p["B"] is None:
+                x[p["V"]] += sla.cho_solve(p["chol"], r)
+            else:                                    # clamped: correction in span(B)
+                x[p["V"]] += p["B"] @ sla.cho_solve(p["chol"], p["B"].T @ r)
     return x
 
 
