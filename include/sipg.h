@@ -90,7 +90,18 @@ typedef enum {
    * Sec. 3.1 makes for this kernel), then every patch of the colour adds its
    * correction: same-colour patches share faces but no DoFs, so inside a
    * colour the corrections are additive. */
-  SIPG_SMOOTHER_FULL = 2
+  SIPG_SMOOTHER_FULL = 2,
+  /* The paper's clamped kernel (Sec. 3.1, Table 2 right): V_j is the
+   * functions on the patch cells whose value and normal derivative vanish on
+   * the patch boundary inside the domain ((2k-2)^d of them for an interior
+   * patch; no condition at a patch end on the domain boundary).  All face
+   * terms of the patch boundary vanish for these test functions, so the
+   * residual is exact.  The paper spans V_j by a Hermite-type basis; this
+   * library keeps the Gauss-Lobatto Lagrange basis and applies the same
+   * subspace correction (B (B^T A_D B)^{-1} B^T R_D r by fast
+   * diagonalisation on the subspace), with the full kernel's launch
+   * structure.  Needs degree >= 2. */
+  SIPG_SMOOTHER_CLAMPED = 3
 } sipg_smoother;
 
 typedef struct {

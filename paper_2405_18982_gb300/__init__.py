@@ -12,11 +12,12 @@ import ctypes
 from dataclasses import dataclass
 
 from . import _binding as B
-from ._binding import (SIPG_FP32, SIPG_FP64, SIPG_SMOOTHER_CONSISTENT, SIPG_SMOOTHER_FULL,
-                       SIPG_SMOOTHER_PAPER, SipgError, load)
+from ._binding import (SIPG_FP32, SIPG_FP64, SIPG_SMOOTHER_CLAMPED, SIPG_SMOOTHER_CONSISTENT,
+                       SIPG_SMOOTHER_FULL, SIPG_SMOOTHER_PAPER, SipgError, load)
 
 __all__ = ["Params", "SIPG", "SIPGBatch", "SipgError", "SIPG_FP64", "SIPG_FP32",
-           "SIPG_SMOOTHER_CONSISTENT", "SIPG_SMOOTHER_PAPER", "SIPG_SMOOTHER_FULL", "load", "build"]
+           "SIPG_SMOOTHER_CONSISTENT", "SIPG_SMOOTHER_PAPER", "SIPG_SMOOTHER_FULL",
+           "SIPG_SMOOTHER_CLAMPED", "load", "build"]
 
 
 def build(force=False, verbose=False):

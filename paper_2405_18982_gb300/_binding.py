@@ -27,6 +27,7 @@ SIPG_FP32 = 1
 SIPG_SMOOTHER_CONSISTENT = 0
 SIPG_SMOOTHER_PAPER = 1
 SIPG_SMOOTHER_FULL = 2
+SIPG_SMOOTHER_CLAMPED = 3
 SIPG_GMRES_MAX_RESTART = 64
 
 

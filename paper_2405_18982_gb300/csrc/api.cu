@@ -663,8 +663,9 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   if (!(p->penalty_factor > 0.0) || !isfinite(p->penalty_factor)) return SIPG_EINVAL;
   if (p->vcycle_precision != SIPG_FP64 && p->vcycle_precision != SIPG_FP32) return SIPG_EINVAL;
   if (p->smoother != SIPG_SMOOTHER_CONSISTENT && p->smoother != SIPG_SMOOTHER_PAPER &&
-      p->smoother != SIPG_SMOOTHER_FULL)
+      p->smoother != SIPG_SMOOTHER_FULL && p->smoother != SIPG_SMOOTHER_CLAMPED)
     return SIPG_EINVAL;
+  if (p->smoother == SIPG_SMOOTHER_CLAMPED && p->degree < 2) return SIPG_EINVAL;  // empty clamped space
   if (p->nrhs < 1 || p->nrhs > 65535) return SIPG_EINVAL;
   const int n = p->degree + 1;
   const int L = p->n_levels - 1;
@@ -812,7 +813,8 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
   SIPG_CHECK(cudaMemcpyAsync(h->hc32.data(), h->c32(0), sizeof(LevelConst<float>) * nl, cudaMemcpyDeviceToHost, s),
              "constants D2H");
   SIPG_CHECK(cudaStreamSynchronize(s), "setup sync");
-  if (h->autotune && h->prm.smoother != SIPG_SMOOTHER_FULL) {  // the full kernel has one launch path
+  // the full and clamped kernels have one launch path
+  if (h->autotune && h->prm.smoother != SIPG_SMOOTHER_FULL && h->prm.smoother != SIPG_SMOOTHER_CLAMPED) {
     const sipg_status st = h->prm.vcycle_precision == SIPG_FP32 ? tune_T<float>(h, s) : tune_T<double>(h, s);
     if (st) return st;
   }

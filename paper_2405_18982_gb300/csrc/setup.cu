@@ -282,8 +282,9 @@ __device__ double l_hi_entry(const LevelConst<double>& c, int k, int i, int j) {
 }
 
 __global__ void setup_levels_kernel(LevelConst<double>* out, int k, int N_finest, int n_levels,
-                                    double kappa, double eta, int paper_residual, double* scratch,
+                                    double kappa, double eta, int smoother, double* scratch,
                                     int* status) {
+  const bool paper_residual = smoother == SIPG_SMOOTHER_PAPER;
   const int l = blockIdx.x;
   const int L = n_levels - 1;
   const int n = k + 1;
@@ -386,17 +387,60 @@ __global__ void setup_levels_kernel(LevelConst<double>* out, int k, int N_finest
       c.lam[t][r] = (r < p) ? lam[r] : 0.0;
       for (int s = 0; s < SIPG_MAXP; ++s) c.S[t][r][s] = (r < p && s < p) ? Ss[r * SIPG_MAXP + s] : 0.0;
     }
-    // full kernel: the same eigenproblem on all P patch nodes
-    for (int r = 0; r < P; ++r)
-      for (int s = 0; s < P; ++s) {
-        As[r * SIPG_MAXP + s] = Lp[r][s];
-        Bs[r * SIPG_MAXP + s] = Mp[r][s];
+    // Full kernel: the same eigenproblem on all P patch nodes.  Clamped
+    // kernel: on the subspace of patch functions with v = v' = 0 at each
+    // patch end inside the domain, spanned by the columns of Bc: one column
+    // per free coefficient f, with the two end coefficients of that end
+    // eliminated (v = 0 fixes the end node; v' = 0 then fixes its
+    // neighbour: sum_j phi_j'(end) c_j = 0).  Sf = Bc S (P x m, zero columns
+    // beyond m) and lamf = 1 beyond m, so the full-kernel patch kernel
+    // applies (Bc S) Lambda^{-1} (Bc S)^T = Bc (Bc^T A_D Bc)^{-1} Bc^T.
+    const bool clamped = smoother == SIPG_SMOOTHER_CLAMPED;
+    double Bc[SIPG_MAXP][SIPG_MAXP];
+    int mc = 0;
+    if (clamped) {
+      const bool lo = !(t & 1), hi = !(t & 2);
+      for (int f = 0; f < P; ++f) {
+        if (lo && f < 2) continue;
+        if (hi && f >= P - 2) continue;
+        for (int r = 0; r < P; ++r) Bc[r][mc] = (r == f) ? 1.0 : 0.0;
+        if (lo && f < n) Bc[1][mc] = -B.D[0][f] / B.D[0][1];
+        if (hi && f >= n) Bc[P - 2][mc] = -B.D[n - 1][f - n] / B.D[n - 1][n - 2];
+        ++mc;
       }
-    ok = generalised_eigen(P, As, Bs, SIPG_MAXP, Ss, lam, W1, W2);
+      for (int r = 0; r < mc; ++r)
+        for (int s = 0; s < mc; ++s) {
+          double a = 0.0, m = 0.0;
+          for (int i = 0; i < P; ++i)
+            for (int j = 0; j < P; ++j) {
+              a += Bc[i][r] * Lp[i][j] * Bc[j][s];
+              m += Bc[i][r] * Mp[i][j] * Bc[j][s];
+            }
+          As[r * SIPG_MAXP + s] = a;
+          Bs[r * SIPG_MAXP + s] = m;
+        }
+    } else {
+      mc = P;
+      for (int r = 0; r < P; ++r)
+        for (int s = 0; s < P; ++s) {
+          As[r * SIPG_MAXP + s] = Lp[r][s];
+          Bs[r * SIPG_MAXP + s] = Mp[r][s];
+        }
+    }
+    ok = mc > 0 && generalised_eigen(mc, As, Bs, SIPG_MAXP, Ss, lam, W1, W2);
     if (!ok) atomicExch(status, 1);
     for (int r = 0; r < SIPG_MAXP; ++r) {
-      c.lamf[t][r] = (r < P) ? lam[r] : 0.0;
-      for (int s = 0; s < SIPG_MAXP; ++s) c.Sf[t][r][s] = (r < P && s < P) ? Ss[r * SIPG_MAXP + s] : 0.0;
+      c.lamf[t][r] = (r < mc) ? lam[r] : 1.0;
+      for (int s = 0; s < SIPG_MAXP; ++s) {
+        double v = 0.0;
+        if (r < P && s < mc) {
+          if (clamped)
+            for (int q = 0; q < mc; ++q) v += Bc[r][q] * Ss[q * SIPG_MAXP + s];
+          else
+            v = Ss[r * SIPG_MAXP + s];
+        }
+        c.Sf[t][r][s] = v;
+      }
     }
   } else if (t == 4 && l == 0) {
     // coarsest level: global 1D SIPG matrix and mass, N n x N n
@@ -491,8 +535,8 @@ cudaError_t launch_setup(sipg_handle* h, cudaStream_t s) {
   double* scratch = reinterpret_cast<double*>(h->ws + h->off_scratch_setup + 256);
   cudaMemsetAsync(status, 0, sizeof(int), s);
   setup_levels_kernel<<<nl, 32, 0, s>>>(h->c64(0), h->prm.degree, 1 << h->prm.log2_cells, nl,
-                                        h->prm.kappa, h->prm.penalty_factor,
-                                        h->prm.smoother == SIPG_SMOOTHER_PAPER ? 1 : 0, scratch, status);
+                                        h->prm.kappa, h->prm.penalty_factor, h->prm.smoother, scratch,
+                                        status);
   constants_to_float_kernel<<<nl, 256, 0, s>>>(h->c64(0), h->c32(0));
   h->launches += 2;
   return cudaGetLastError();

@@ -9,6 +9,14 @@
 // share faces but no DoFs, so their corrections are independent and the
 // pass is race-free.
 //
+// The clamped kernel (Sec. 3.1) runs the same passes: its constants are the
+// columns B S of the clamped subspace basis B times the eigenvectors of the
+// projected 1D patch matrices, padded with zero columns (eigenvalue 1), so
+// the patch kernel applies B (B^T A_D B)^{-1} B^T to the patch residual;
+// same-colour clamped patches do not see each other's DoFs in their
+// residuals, so one global residual per colour gives the multiplicative
+// result.
+//
 // Patch kernel: a patch's P^d residual values (P = 2n) are staged in shared
 // memory in patch-lexicographic order (direction 0 fastest); each thread owns
 // one line per direction and applies S^T along directions 0..d-1, the

@@ -42,7 +42,7 @@ cudaError_t step_dim(const sipg_handle* h, int level, int reverse, const T* b, T
 template <typename T>
 cudaError_t launch_smooth_colour(const sipg_handle* h, int level, int colour, const T* b, T* x,
                                  cudaStream_t s) {
-  if (h->prm.smoother == SIPG_SMOOTHER_FULL) {
+  if (h->prm.smoother == SIPG_SMOOTHER_FULL || h->prm.smoother == SIPG_SMOOTHER_CLAMPED) {
     int nl = 0;
     return launch_full_colour<T>(h, level, colour, b, x, s, &nl);
   }
@@ -57,7 +57,7 @@ template <typename T>
 cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s,
                                int* launches) {
   const int nc = 1 << h->prm.dim;
-  if (h->prm.smoother == SIPG_SMOOTHER_FULL) {
+  if (h->prm.smoother == SIPG_SMOOTHER_FULL || h->prm.smoother == SIPG_SMOOTHER_CLAMPED) {
     *launches = 0;
     for (int i = 0; i < nc; ++i) {
       int nl = 0;

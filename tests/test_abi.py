@@ -52,6 +52,13 @@ def test_host_only_calls_without_gpu(lib):
     assert lib.sipg_create(ctypes.byref(bad), ctypes.byref(h)) == -1
     bad = sipg_params(3, 3, 3, 2, -1.0, 1.0, 0, 0, 1, 0)  # kappa <= 0
     assert lib.sipg_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad = sipg_params(2, 1, 3, 2, 1.0, 1.0, 0, 3, 1, 0)   # clamped kernel with k = 1: empty space
+    assert lib.sipg_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad = sipg_params(2, 2, 3, 2, 1.0, 1.0, 0, 4, 1, 0)   # no smoother 4
+    assert lib.sipg_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    ok = sipg_params(2, 2, 3, 2, 1.0, 1.0, 0, 3, 1, 0)
+    assert lib.sipg_create(ctypes.byref(ok), ctypes.byref(h)) == 0
+    lib.sipg_destroy(h)
     good = sipg_params(3, 3, 6, 6, 1.0, 1.0, 1, 0, 1, 0)
     assert lib.sipg_create(ctypes.byref(good), ctypes.byref(h)) == 0 and h.value
     assert lib.sipg_ndofs(h, 5) == 64 ** 3 * 64
