@@ -11,12 +11,13 @@
  *   boundary faces (h- := h+), homogeneous Dirichlet conditions imposed
  *   weakly.  Matrix form A x = b.
  *
- * Solver (Sec. 3): flexible CG on the finest level, preconditioned by one
- * multigrid V-cycle (Sec. 3) with the colourised multiplicative vertex-patch
- * smoother (Algorithm 1), fast-diagonalisation local solvers (Eqs. inverse2d,
- * inverse3d, fast_inverse), canonical-embedding prolongation and its
- * transpose as restriction, and an exact coarse solve.  The V-cycle may run
- * in FP32 inside the FP64 outer solver (Sec. 5.2).
+ * Solver (Sec. 3): flexible CG (or the paper's GMRES, sipg_gmres_solve) on
+ * the finest level, preconditioned by one multigrid V-cycle (Sec. 3) with the
+ * colourised multiplicative vertex-patch smoother (Algorithm 1; Dirichlet,
+ * full or clamped local solver, sipg_smoother), fast-diagonalisation local
+ * solvers (Eqs. inverse2d, inverse3d, fast_inverse), canonical-embedding
+ * prolongation and its transpose as restriction, and an exact coarse solve.
+ * The V-cycle may run in FP32 inside the FP64 outer solver (Sec. 5.2).
  *
  * Data layout (Sec. 4.1): every vector is cell-wise lexicographic.  On a level
  * with N cells per direction and n = k+1 nodes per direction, DoF (cell c,
