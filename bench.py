@@ -155,6 +155,26 @@ def apply_counts(dim, k, N, s_bytes):
 
 
 # ----------------------------------------------------------------- our arm
+def reduce_over_ranks(dist, v, op, device):
+    """One float reduced over all ranks ("max" or "sum"); v itself on one rank."""
+    import torch
+    if dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_mdofs(dist, device, ndofs, vcycles, seconds):
+    """Whole-job MDoF/s per V-cycle: every rank solves its own replica of the
+    problem (ndofs DoFs, `vcycles` V-cycles in `seconds` on this rank); the
+    units of all ranks divided by the slowest rank's time.  Returns (value,
+    slowest time)."""
+    t_max = reduce_over_ranks(dist, seconds, "max", device)
+    total = reduce_over_ranks(dist, float(vcycles), "sum", device)
+    return ndofs * total / t_max / 1e6, t_max
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -178,18 +198,10 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(dist, v, "max", dev)
 
     def sum_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(dist, v, "sum", dev)
 
     mk = lambda prec: SIPG(Params(dim=DIM, degree=K, log2_cells=LOG2N, n_levels=NLEV,
                                   vcycle_precision=prec, use_graphs=1), device=dev)
@@ -229,9 +241,7 @@ def run_ours(args):
     clk = clocks.stop()
     t_mix = ev0.elapsed_time(ev1) / 1e3
     launches = s_mix.launch_count() - l0 + args.steps  # + the torch zero_ per step
-    t_mix_max = max_over_ranks(t_mix)
-    total_vc = sum_over_ranks(float(sum(iters)))
-    value = n * total_vc / t_mix_max / 1e6
+    value, t_mix_max = whole_job_mdofs(dist, dev, n, sum(iters), t_mix)
     rel_res_mix = info.rel_residual
 
     # solution error of the mixed solve against the FP64 solve (reported)
