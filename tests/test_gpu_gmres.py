@@ -114,6 +114,16 @@ def test_gmres_errors():
     multi = make(2, 2, 3, 2, nrhs=2)
     with pytest.raises(SipgError):
         multi.gmres_solve(dev(np.zeros(2 * n)), dev(np.zeros(2 * n)))
+    # a non-finite right-hand side ends in a clean status, and the handle
+    # stays usable
+    bad = inputs.normal(741, n)
+    bad[5] = np.nan
+    x.zero_()
+    with pytest.raises(SipgError) as err:
+        s.gmres_solve(dev(bad), x, rtol=1e-8, maxit=10)
+    assert err.value.status == B.SIPG_EBREAKDOWN
+    x.zero_()
+    assert s.gmres_solve(b, x, rtol=1e-8, maxit=100).status == 0
 
 
 @pytest.mark.parametrize("prec", [SIPG_FP64, SIPG_FP32], ids=["fp64", "mixed"])
