@@ -175,7 +175,9 @@ sipg_status sipg_apply_penalty(sipg_handle* h, const double* x, double* y, void*
 /* One colour pass of Algorithm 1 on `level`: for all vertex patches j of
  * colour c (c = sum_e (v_e mod 2) 2^e, v the vertex index), in parallel,
  * r_j = local residual, x[V_j] += (S (x) S (x) S) Lambda^{-1} (S^T (x) ...) r_j.
- * x is updated in place. */
+ * x is updated in place.  With the full or clamped kernel the pass first
+ * writes b - A x for the whole level into the level's residual buffer of the
+ * workspace (so passes of one handle must not overlap on the GPU). */
 sipg_status sipg_smooth_colour(sipg_handle* h, int level, int prec, int colour, const void* b,
                                void* x, void* stream);
 /* One smoothing step S_l(x, b): colours 0..2^d-1, or 2^d-1..0 if reverse. */
