@@ -666,8 +666,30 @@ def _oracle_iteration(H, r):
     return z, q
 
 
+SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
 def cpu_baseline(seconds=12.0):
-    import numpy as np
+    """The oracle timed on one host core: run in a fresh interpreter whose BLAS
+    and OpenMP pools are limited to one thread before NumPy loads (this process
+    has loaded them already)."""
+    env = dict(os.environ, **SINGLE_THREAD_ENV)
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._cpu_baseline_here(%r)))" % (ROOT, float(seconds)))
+    try:
+        res = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                             timeout=seconds * 10 + 300)
+        if res.returncode == 0:
+            return json.loads(res.stdout.strip().splitlines()[-1])
+    except (OSError, ValueError, subprocess.TimeoutExpired):
+        pass
+    out = _cpu_baseline_here(seconds)  # threads not pinned in this process
+    out["sample"] += " (in-process: BLAS threads not pinned)"
+    out["cores"] = None
+    return out
+
+
+def _cpu_baseline_here(seconds):
     H, b = _oracle_sample()
     nd = H.A.shape[0]
     r = b.copy()
@@ -687,6 +709,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    os.environ.update(SINGLE_THREAD_ENV)  # one core: set before NumPy loads
     H, b = _oracle_sample()
     nd = H.A.shape[0]
     r = b.copy()
