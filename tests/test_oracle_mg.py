@@ -7,7 +7,7 @@ import pytest
 import scipy.linalg as sla
 
 from oracle.assembly import assemble, mass_matrix_cell
-from oracle.basis import gauss_lobatto, lagrange_values
+from oracle.basis import gauss_lobatto
 from oracle.direct import GlobalFD, one_d_matrices
 from oracle.layout import node_coordinates
 from oracle.mg import (Hierarchy, Level, fcg, fractional_iterations, mg_solve,
