@@ -563,3 +563,24 @@ def test_gmres_clamped_kernel_near_table2():
         assert printed / 2 <= nus[k] <= printed * 2, (k, nus[k], printed)
         assert nus[k] > dirichlet[L - 2, k - 2]      # the paper's ordering at low degree
     assert nus[4] < nus[3]
+
+
+def test_clamped_space_closed_form_for_q2():
+    # k = 2, interior patch: on the low cell a quadratic with v = v' = 0 at
+    # its low end is a multiple of x^2, on the high cell one with v = v' = 0
+    # at its high end is a multiple of (1 - x)^2; in the Gauss-Lobatto
+    # Lagrange coefficients (nodes 0, 1/2, 1) these are (0, 1/4, 1) and
+    # (1, 1/4, 0).  With a domain-boundary end the space gains that end's
+    # value and derivative (2k and 2k + 2 functions).
+    from oracle.mg import clamped_basis_1d
+    B = clamped_basis_1d(2, False, False)
+    expect = np.array([[0, 0.25, 1, 0, 0, 0], [0, 0, 0, 1, 0.25, 0]], dtype=float).T
+    assert B.shape == (6, 2)
+    proj = B @ (B.T @ expect)                      # expect lies in span(B)
+    assert np.abs(proj - expect).max() < 1e-13
+    assert np.allclose(B.T @ B, np.eye(2), atol=1e-13)
+    for k in range(2, 8):
+        assert clamped_basis_1d(k, False, False).shape[1] == 2 * k - 2
+        assert clamped_basis_1d(k, True, False).shape[1] == 2 * k
+        assert clamped_basis_1d(k, False, True).shape[1] == 2 * k
+        assert clamped_basis_1d(k, True, True).shape[1] == 2 * k + 2
