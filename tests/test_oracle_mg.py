@@ -584,3 +584,15 @@ def test_clamped_space_closed_form_for_q2():
         assert clamped_basis_1d(k, True, False).shape[1] == 2 * k
         assert clamped_basis_1d(k, False, True).shape[1] == 2 * k
         assert clamped_basis_1d(k, True, True).shape[1] == 2 * k + 2
+
+
+def test_full_kernel_at_most_three_steps_for_degree_four():
+    # Sec. 3.3 on Table 1: for degrees 4 and higher the full kernel converges
+    # (GMRES to 1e-8, f = 1) in at most three steps
+    from oracle.assembly import rhs_from_nodal
+    from oracle.mg import gmres
+    for k in (4, 5):
+        H = Hierarchy(3, k, 4, 2, variant="full")
+        b = rhs_from_nodal(3, k, 4, np.ones(H.A.shape[0]))
+        _, hist = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=10)
+        assert len(hist) - 1 <= 3 and hist[-1] <= 1e-8 * hist[0], (k, hist)
