@@ -596,3 +596,15 @@ def test_full_kernel_at_most_three_steps_for_degree_four():
         b = rhs_from_nodal(3, k, 4, np.ones(H.A.shape[0]))
         _, hist = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=10)
         assert len(hist) - 1 <= 3 and hist[-1] <= 1e-8 * hist[0], (k, hist)
+
+
+def test_local_space_dimensions_for_q3():
+    # Sec. 3.3: for Q3 the local space of an interior patch has 8^3 functions
+    # for the full kernel, 6^3 for the Dirichlet kernel, 4^3 for the clamped
+    N = 6
+    interior = lambda p: all(1 < p["vertex"][e] < N - 1 for e in range(3))
+    for variant, dim_vj in (("full", 8 ** 3), ("consistent", 6 ** 3), ("clamped", 4 ** 3)):
+        lev = Level(3, 3, N, variant=variant)
+        p = next(p for p in lev.patches if interior(p))
+        size = p["B"].shape[1] if p["B"] is not None else len(p["V"])
+        assert size == dim_vj, (variant, size)
