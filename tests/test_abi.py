@@ -123,3 +123,26 @@ def test_tuning_query_without_gpu(lib):
     assert lib.sipg_tuning(h, 3, 1, ctypes.byref(path), ctypes.byref(tile)) == -1  # no level 3
     assert lib.sipg_tuning(h, 0, 5, ctypes.byref(path), ctypes.byref(tile)) == -1  # bad precision
     lib.sipg_destroy(h)
+
+
+def test_smoother_choices_and_gmres_sizes_without_gpu(lib):
+    from paper_2405_18982_gb300._binding import SIGNATURES, sipg_params
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    h = ctypes.c_void_p()
+    for dim in (2, 3):
+        for k in range(1, 8):
+            for sm in range(4):
+                p = sipg_params(dim, k, 3, 2, 1.0, 1.0, 0, sm, 1, 0)
+                st = lib.sipg_create(ctypes.byref(p), ctypes.byref(h))
+                if sm == 3 and k < 2:
+                    assert st == -1 and not h.value
+                    continue
+                assert st == 0, (dim, k, sm)
+                nf = lib.sipg_ndofs(h, 1)
+                sizes = [lib.sipg_gmres_workspace_bytes(h, m) for m in (1, 2, 30, 64)]
+                assert all(a < b for a, b in zip(sizes, sizes[1:]))
+                for m, size in zip((1, 2, 30, 64), sizes):
+                    assert size >= (2 * m + 1) * nf * 8
+                lib.sipg_destroy(h)
