@@ -134,13 +134,13 @@ def test_smoother_choices_and_gmres_sizes_without_gpu(lib):
     for dim in (2, 3):
         for k in range(1, 8):
             for sm in range(4):
-                p = sipg_params(dim, k, 3, 2, 1.0, 1.0, 0, sm, 1, 0)
+                p = sipg_params(dim, k, 3, 3, 1.0, 1.0, 0, sm, 1, 0)   # coarsest level 2 cells
                 st = lib.sipg_create(ctypes.byref(p), ctypes.byref(h))
                 if sm == 3 and k < 2:
                     assert st == -1 and not h.value
                     continue
                 assert st == 0, (dim, k, sm)
-                nf = lib.sipg_ndofs(h, 1)
+                nf = lib.sipg_ndofs(h, 2)
                 sizes = [lib.sipg_gmres_workspace_bytes(h, m) for m in (1, 2, 30, 64)]
                 assert all(a < b for a, b in zip(sizes, sizes[1:]))
                 for m, size in zip((1, 2, 30, 64), sizes):
