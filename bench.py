@@ -44,11 +44,36 @@ WORKLOAD = ("3D SIPG Poisson, unit cube, 64^3 cells, 6 levels, Q3 GLL (16.8M DoF
             "gamma = 2k(k+1)/h, f = manufactured 3pi^2 prod sin + U[-1,1] noise (seed 2), "
             "FP32 V-cycle (1+1 vertex-patch smoothing) inside FP64 flexible CG to 1e-10; "
             "plain FP64 solve timed beside it")
-# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu
-# capture of this kernel (summary under profiles/); None when
-# the kernel has changed since that capture
-TRAFFIC_INTERIOR_COLOUR0 = 142829824  # 127.70 MB read + 15.13 MB written
+# DRAM bytes (read + write) of one launch of a kernel, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; summaries under profiles/)
+# of the library built from sources whose digest is recorded here; reported
+# as null once any of those sources has changed since the capture
+TRAFFIC = {
+    "colour_pass": {"bytes": None, "sha": None,
+                    "sources": ["smooth_i_d3_f32_a.cu", "smoother_impl.cuh", "smooth_int3.cuh", "tensor_ops.cuh",
+                                "sipg_internal.cuh"]},
+    "fp64_apply": {"bytes": None, "sha": None,
+                   "sources": ["apply.cu", "apply3.cuh", "tensor_ops.cuh", "sipg_internal.cuh"]},
+}
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+
+
+def source_digest(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2405_18982_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(name):
+    t = TRAFFIC[name]
+    if t["bytes"] is None or t["sha"] != source_digest(t["sources"]):
+        return None
+    return t["bytes"]
+
+
 # peaks (MEASURED_PEAKS.json for HBM; ALU peaks from unit counts x max SM clock)
 SMS, FP32_LANES, FP64_UNITS, SM_MAX_MHZ = 152, 128, 2, 2070.0
 
@@ -126,11 +151,57 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- algorithmic counts
+def _lr_nz(nn, a, c):
+    """Structural nonzero (a, c) of the 1D patch SIPG matrix on the two patch
+    cells (2nn nodes): the own cell is dense; across the vertex the coupling
+    is rank two (the vertex node's row sees the whole other cell, every other
+    row only the other cell's node next to the vertex)."""
+    return (a // nn == c // nn) or ((a == nn - 1 or c == nn) if a < nn else (a == nn or c == nn - 1))
+
+
+def colour_pass_schedule_flops(dim, k, packed=True):
+    """Flops per interior patch of the colour-pass kernels' sum-factorised
+    schedule (Algorithm 1, Eqs. inverse2d / inverse3d): the local residual by
+    line sweeps of the 1D patch mass (diagonal plus rank one per cell) and
+    SIPG rows (structural zeros skipped; FP32 pairs two rows per packed FMA
+    over the union of their nonzeros), then the six (four in 2D) p x p
+    eigenvector sweeps and the eigenvalue scaling.  An FMA counts 2."""
+    nn, P, p, off = k + 1, 2 * (k + 1), 2 * k, 1
+
+    def mass(acc):
+        return 2 * (2 * nn - 1) + p * (4 if acc else 3)
+
+    def sipg():
+        f = 0
+        if packed:
+            for q in range(p // 2):
+                a0 = 2 * q + off
+                nz = sum(1 for c in range(P) if _lr_nz(nn, a0, c) or _lr_nz(nn, a0 + 1, c))
+                f += 2 + 4 * nz
+        else:
+            for r in range(p):
+                f += 1 + 2 * sum(1 for c in range(P) if _lr_nz(nn, r + off, c))
+        return f
+
+    st = p * (2 * p - 1)
+    if dim == 3:
+        x = P * P * (mass(False) + sipg()) + 4 * P * mass(False)
+        y = p * P * (mass(False) + sipg() + mass(True)) + 2 * p * mass(False)
+        z = p * p * (sipg() + mass(True) + p)
+        return x + y + z + 6 * p * p * st + p ** 3
+    x = P * (mass(False) + sipg()) + 2 * mass(False)
+    y = p * (sipg() + mass(True) + 1)
+    return x + y + 4 * p * st + p ** 2
+
+
 def smoother_counts(dim, k, N, colour, s_bytes):
-    """Algorithmic flops and HBM bytes of one colour pass (Algorithm 1 with
-    fast diagonalisation), interior-patch formulas: residual
-    4pP^3 + 6p^2P^2 + 4p^3P, FD 4d p^(d+1) + p^d (P = 2(k+1), p = 2k);
-    bytes = read x on the patch cells, read b and read-modify-write x on V_j."""
+    """One colour pass over its interior patches.  Returns (survey flops,
+    schedule flops, bytes, patches): survey = the reference count with dense
+    1D operators, residual 4pP^3 + 6p^2P^2 + 4p^3P (2D 4pP^2 + 4p^2P) plus FD
+    4d p^(d+1) + p^d per patch (P = 2(k+1), p = 2k); schedule =
+    colour_pass_schedule_flops (the work the kernels do); bytes = the
+    colour-pass model (P^d + 2p^d) s per patch: x read on the patch cells,
+    b read and x written on V_j."""
     n = k + 1
     P, p = 2 * n, 2 * k
     npatch = 1
@@ -138,19 +209,27 @@ def smoother_counts(dim, k, N, colour, s_bytes):
         npatch *= N // 2 if (colour >> e) & 1 else N // 2 - 1
     if dim == 3:
         fl = 4 * p * P ** 3 + 6 * p * p * P * P + 4 * p ** 3 * P + 4 * dim * p ** (dim + 1) + p ** dim
-        by = (P ** 3 + 3 * p ** 3) * s_bytes
     else:
         fl = 4 * p * P * P + 4 * p * p * P + 4 * dim * p ** (dim + 1) + p ** dim
-        by = (P ** 2 + 3 * p ** 2) * s_bytes
-    return npatch * fl, npatch * by, npatch
+    by = (P ** dim + 2 * p ** dim) * s_bytes
+    sched = colour_pass_schedule_flops(dim, k, packed=(s_bytes == 4))
+    return npatch * fl, npatch * sched, npatch * by, npatch
 
 
 def apply_counts(dim, k, N, s_bytes):
-    """Apply: 3 normal contractions with rank-2 neighbour terms + 5 (3D) mass
-    contractions per DoF; bytes = read x + write y."""
+    """Operator apply y = A x (Sec. 2.2, sum-factorised): flops of the
+    kernel's schedule per DoF -- d normal sweeps with the n x n 1D blocks
+    (2n each), the rank-two neighbour couplings along each direction where a
+    neighbour exists ((8n + 2)/n per DoF), and the mass sweeps as diagonal
+    plus rank one (3D: 3 plain (5 - 1/n) + 2 accumulating (6 - 1/n); 2D: one
+    of each); bytes = read x + write y.  3D interior: 6n + 51 + 1/n."""
     n = k + 1
     nd = N ** dim * n ** dim
-    per = (8 * 2 * n + 2 * dim * 4) if dim == 3 else (4 * 2 * n + 2 * dim * 4)
+    nb = dim * (8 * n + 2) / n * (N - 1) / N
+    if dim == 3:
+        per = 6 * n + nb + 3 * (5 - 1 / n) + 2 * (6 - 1 / n)
+    else:
+        per = 4 * n + nb + (5 - 1 / n) + (6 - 1 / n)
     return nd * per, nd * 2 * s_bytes
 
 
@@ -218,8 +297,7 @@ def run_ours(args):
 
     # ---- warm-up (also captures the CUDA graphs)
     for _ in range(args.warmup):
-        x.zero_()
-        s_mix.solve(b, x, rtol=RTOL, maxit=200)
+        s_mix.solve(b, x, rtol=RTOL, maxit=200, zero_start=True)
     torch.cuda.synchronize()
 
     # ---- timed region: K mixed-precision solves
@@ -232,30 +310,27 @@ def run_ours(args):
     iters = []
     ev0.record(stream)
     for _ in range(args.steps):
-        x.zero_()
-        info = s_mix.solve(b, x, rtol=RTOL, maxit=200)
+        info = s_mix.solve(b, x, rtol=RTOL, maxit=200, zero_start=True)
         iters.append(info.iterations)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     t_mix = ev0.elapsed_time(ev1) / 1e3
-    launches = s_mix.launch_count() - l0 + args.steps  # + the torch zero_ per step
+    launches = s_mix.launch_count() - l0
     value, t_mix_max = whole_job_mdofs(dist, dev, n, sum(iters), t_mix)
     rel_res_mix = info.rel_residual
 
     # solution error of the mixed solve against the FP64 solve (reported)
     x64 = torch.zeros_like(f)
     for _ in range(max(1, min(2, args.warmup))):
-        x64.zero_()
-        s_64.solve(b, x64, rtol=RTOL, maxit=200)
+        s_64.solve(b, x64, rtol=RTOL, maxit=200, zero_start=True)
     torch.cuda.synchronize()
     k64 = max(1, (args.steps + 1) // 2)
     ev0.record(stream)
     it64 = []
     for _ in range(k64):
-        x64.zero_()
-        i64 = s_64.solve(b, x64, rtol=RTOL, maxit=200)
+        i64 = s_64.solve(b, x64, rtol=RTOL, maxit=200, zero_start=True)
         it64.append(i64.iterations)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -284,42 +359,97 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_vc64 = ev0.elapsed_time(ev1) / 1e3 / 3
 
-    # ---- dominant kernel: the finest-level FP32 interior colour pass.  Colour
-    # 0 (all vertex indices even) has no patch on the domain boundary, so
-    # sipg_smooth_colour launches exactly one kernel (smooth_int3_kernel<4,
-    # float, interior>) on the calling stream; CUDA events around repeated
-    # launches give its average duration.
+    # ---- dominant kernels.  (1) The finest-level FP32 interior colour pass:
+    # colour 0 (all vertex indices even) has no patch on the domain boundary,
+    # so sipg_smooth_colour launches exactly one kernel
+    # (smooth_int3_kernel<4, float, interior>) on the calling stream; CUDA
+    # events around repeated launches give its average duration.  (2) The
+    # FP64 operator apply of the outer CG (apply_kernel<3, 4, double>), one
+    # launch per sipg_apply on the finest level in FP64.
     L = NLEV - 1
     N = 1 << LOG2N
-    nrep = 20
-    for _ in range(3):
-        s_mix.smooth_colour(L, 0, bf, xf)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(nrep):
-        s_mix.smooth_colour(L, 0, bf, xf)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    t_col = ev0.elapsed_time(ev1) / 1e3 / nrep
-    fl_launch, by_launch, npatch0 = smoother_counts(DIM, K, N, 0, 4)
     hbm, hbm_src = measured_peaks()
-    achieved_tf = fl_launch / t_col / 1e12
-    achieved_gb = by_launch / t_col / 1e9
-    peak_tf = fp32_peak_tflops()
-    frac_alu = achieved_tf / peak_tf
-    frac_hbm = achieved_gb / hbm
-    if fl_launch / (peak_tf * 1e12) >= by_launch / (hbm * 1e9):
-        roof = {"bound": "alu", "achieved": round(achieved_tf, 3), "peak": round(peak_tf, 2),
-                "unit": "TFLOP/s", "frac": round(frac_alu, 4),
-                "peak_source": "FP32: 152 SMs x 128 lanes x 2 x 2070 MHz (unit counts x max clock)"}
-    else:
-        roof = {"bound": "hbm", "achieved": round(achieved_gb, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(frac_hbm, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
-    roof.update({"kernel": "smooth_int3_kernel<4,float,interior> (finest level, colour 0, %d patches)" % npatch0,
-                 "traffic": TRAFFIC_INTERIOR_COLOUR0, "traffic_source": TRAFFIC_SOURCE,
-                 "avg_launch_us": round(t_col * 1e6, 2),
-                 "algorithmic_flops_per_launch": int(fl_launch), "algorithmic_bytes_per_launch": int(by_launch),
-                 "hbm_frac": round(frac_hbm, 4), "alu_frac": round(frac_alu, 4)})
+    peak32, peak64 = fp32_peak_tflops(), fp64_peak_tflops()
+
+    def launch_time(fn, nrep=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(nrep):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / nrep
+
+    def roofline(kernel, flops, nbytes, t, peak_tf, alu_name, traffic, extra):
+        t_alu = flops / (peak_tf * 1e12)
+        t_hbm = nbytes / (hbm * 1e9)
+        ach_tf, ach_gb = flops / t / 1e12, nbytes / t / 1e9
+        if t_alu >= t_hbm:
+            r = {"bound": "alu", "achieved": round(ach_tf, 3), "peak": round(peak_tf, 3), "unit": "TFLOP/s",
+                 "frac": round(ach_tf / peak_tf, 4),
+                 "peak_source": f"{alu_name}: 152 SMs x unit count x 2 x 2070 MHz (derived)"}
+        else:
+            r = {"bound": "hbm", "achieved": round(ach_gb, 1), "peak": hbm, "unit": "GB/s",
+                 "frac": round(ach_gb / hbm, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
+        r.update({"kernel": kernel, "traffic": traffic,
+                  "traffic_source": TRAFFIC_SOURCE if traffic is not None else
+                  "null: the kernel's sources changed since the last ncu capture",
+                  "avg_launch_us": round(t * 1e6, 2), "algorithmic_flops_per_launch": int(flops),
+                  "algorithmic_bytes_per_launch": int(nbytes),
+                  "hbm_frac": round(ach_gb / hbm, 4), "alu_frac": round(ach_tf / peak_tf, 4)})
+        if traffic is not None:
+            r["traffic_over_algorithmic"] = round(traffic / nbytes, 3)
+        r.update(extra)
+        return r
+
+    t_col = launch_time(lambda: s_mix.smooth_colour(L, 0, bf, xf))
+    fl_survey, fl_sched, by_col, npatch0 = smoother_counts(DIM, K, N, 0, 4)
+    roof = roofline("smooth_int3_kernel<4,float,interior> (finest level, colour 0, %d patches)" % npatch0,
+                    fl_sched, by_col, t_col, peak32, "FP32", measured_traffic("colour_pass"),
+                    {"survey_flops_per_launch": int(fl_survey),
+                     "survey_alu_frac": round(fl_survey / t_col / 1e12 / peak32, 4),
+                     "counts": "flops = kernel schedule (sum-factorised, rank-one mass, structural zeros "
+                               "skipped); bytes = (P^3 + 2p^3) x 4 B per patch"})
+    y64 = torch.zeros_like(b)
+    t_app = launch_time(lambda: s_64.apply(L, b, y64))
+    fl_app, by_app = apply_counts(DIM, K, N, 8)
+    roof_apply = roofline("apply_kernel<3,4,double> (outer CG operator apply, finest level)", fl_app, by_app,
+                          t_app, peak64, "FP64", measured_traffic("fp64_apply"),
+                          {"launches_per_solve": "iterations + 1 (q = A p per iteration, final true residual)",
+                           "counts": "flops per DoF = 6n + 51 + 1/n (3D interior; neighbour terms only where a "
+                                     "neighbour exists); bytes = 2 x 8 B per DoF"})
+
+    # ---- per-operation throughput on this workload (finest level), with the
+    # fraction of each operation's roofline: apply and smoothing step against
+    # max(flop time, byte time) at the peaks above; the V-cycle and the solve
+    # as MDoF/s
+    yf = torch.zeros_like(bf)
+    t_a32 = launch_time(lambda: s_mix.apply(L, bf, yf), 10)
+    t_step = launch_time(lambda: s_mix.smooth(L, bf, xf), 5)
+    fl_a32, by_a32 = apply_counts(DIM, K, N, 4)
+    st_fl, st_by = 0, 0
+    for c in range(2 ** DIM):
+        _, f_c, b_c, _ = smoother_counts(DIM, K, N, c, 4)
+        st_fl, st_by = st_fl + f_c, st_by + b_c
+
+    def op(t, flops=None, nbytes=None, peak_tf=None):
+        o = {"mdofs": round(n / t / 1e6, 1), "us": round(t * 1e6, 2)}
+        if flops is not None:
+            floor = max(flops / (peak_tf * 1e12), nbytes / (hbm * 1e9))
+            o["roofline_frac"] = round(floor / t, 4)
+            o["bound"] = "alu" if flops / (peak_tf * 1e12) >= nbytes / (hbm * 1e9) else "hbm"
+        return o
+
+    per_op = {"apply_fp32": op(t_a32, fl_a32, by_a32, peak32),
+              "apply_fp64": op(t_app, fl_app, by_app, peak64),
+              "smoothing_step_fp32": op(t_step, st_fl, st_by, peak32),
+              "vcycle_fp32": op(t_vc32), "vcycle_fp64": op(t_vc64),
+              "solve_mixed_per_vcycle": op(t_mix_max / sum(iters)),
+              "note": "finest level of this workload; roofline_frac = max(flops / FP peak, bytes / HBM peak) / "
+                      "time with the counts of the roofline objects (smoothing step: interior-patch model for "
+                      "every patch of the 2^d colours)"}
 
     # ---- end to end through the public host-buffer call
     fh = f.detach().cpu().pin_memory()
@@ -357,6 +487,8 @@ def run_ours(args):
                 "fp64_mdofs_per_vcycle_in_solve": round(n * sum(it64) / t_64 / 1e6, 2),
             },
             "roofline": roof,
+            "roofline_fp64_apply": roof_apply,
+            "per_op": per_op,
             "e2e": {"value": round(e2e_value, 2), "unit": "MDoF/s", "h2d_bytes_per_step": n * 8,
                     "d2h_bytes_per_step": n * 8,
                     "note": "sipg_solve_host: pinned f in, b = M f, solve from 0, u out"},
@@ -381,18 +513,20 @@ def run_kernel_only(args):
     pkg.load(pkg.build())
     prec = SIPG_FP64 if args.precision == "fp64" else SIPG_FP32
     dt = torch.float64 if prec == SIPG_FP64 else torch.float32
-    s = SIPG(Params(dim=DIM, degree=K, log2_cells=LOG2N, n_levels=NLEV, vcycle_precision=prec))
+    dim, k, l2 = args.dim, args.degree, args.log2n
+    nlev = args.levels or l2
+    s = SIPG(Params(dim=dim, degree=k, log2_cells=l2, n_levels=nlev, vcycle_precision=prec))
     n = s.ndofs()
     b = torch.from_numpy(inputs.uniform(NOISE_SEED, n)).to("cuda").view(1, n).to(dt)
     x = torch.zeros_like(b)
-    L = NLEV - 1
+    L = nlev - 1
 
     if args.mode == "levels":
         # per-level cost of the V-cycle pieces (smoothing step, residual,
         # transfer) on this workload, CUDA events around each call
         out = {}
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for lev in range(NLEV - 1, 0, -1):
+        for lev in range(nlev - 1, 0, -1):
             nl = s.ndofs(lev)
             bl = torch.from_numpy(inputs.uniform(NOISE_SEED + lev, nl)).to("cuda").view(1, nl).to(dt)
             xl = torch.zeros_like(bl)
@@ -412,13 +546,13 @@ def run_kernel_only(args):
                 e1.record()
                 torch.cuda.synchronize()
                 row[name] = round(e0.elapsed_time(e1) / args.steps * 1e3, 2)
-            out[f"N={1 << (LOG2N - (NLEV - 1 - lev))}"] = row
+            out[f"N={1 << (l2 - (nlev - 1 - lev))}"] = row
         print(json.dumps({"mode": "levels", "precision": args.precision, "us_per_call": out}))
         return
 
     def one():
         if args.mode == "smooth":
-            for c in range(2 ** DIM):
+            for c in (range(2 ** dim) if args.colour < 0 else (args.colour,)):
                 s.smooth_colour(L, c, b, x)
         elif args.mode == "apply":
             s.apply(L, b, x)
@@ -435,8 +569,9 @@ def run_kernel_only(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"mode": args.mode, "precision": args.precision, "ms_per_rep": round(ms, 4),
-                      "launches_per_rep": (2 ** DIM if args.mode == "smooth" else 1)}))
+    print(json.dumps({"mode": args.mode, "precision": args.precision, "dim": dim, "degree": k,
+                      "cells_per_dir": 1 << l2, "levels": nlev, "dofs": n, "colour": args.colour,
+                      "ms_per_rep": round(ms, 4)}))
 
 
 # ----------------------------------------------------------------- batched runs
@@ -669,24 +804,47 @@ def _oracle_iteration(H, r):
 SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
-def cpu_baseline(seconds=12.0):
-    """The oracle timed on one host core: run in a fresh interpreter whose BLAS
-    and OpenMP pools are limited to one thread before NumPy loads (this process
-    has loaded them already)."""
+def _oracle_workers(seconds, count):
+    """`count` fresh single-threaded interpreters, started together, each
+    timing oracle FCG iterations on its own copy of the sample for about
+    `seconds`; returns their JSON results (None on failure)."""
     env = dict(os.environ, **SINGLE_THREAD_ENV)
     code = ("import json, sys; sys.path.insert(0, %r); import bench; "
             "print(json.dumps(bench._cpu_baseline_here(%r)))" % (ROOT, float(seconds)))
-    try:
-        res = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
-                             timeout=seconds * 10 + 300)
-        if res.returncode == 0:
-            return json.loads(res.stdout.strip().splitlines()[-1])
-    except (OSError, ValueError, subprocess.TimeoutExpired):
-        pass
-    out = _cpu_baseline_here(seconds)  # threads not pinned in this process
-    out["sample"] += " (in-process: BLAS threads not pinned)"
-    out["cores"] = None
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, cwd=ROOT, stdout=subprocess.PIPE,
+                              stderr=subprocess.DEVNULL, text=True) for _ in range(count)]
+    out = []
+    for p in procs:
+        try:
+            so, _ = p.communicate(timeout=seconds * 10 + 300)
+            out.append(json.loads(so.strip().splitlines()[-1]) if p.returncode == 0 else None)
+        except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+            p.kill()
+            out.append(None)
     return out
+
+
+def cpu_baseline(seconds=12.0):
+    """The oracle timed on the host cores: one single-threaded interpreter
+    alone (the single-core figure), then one per core at the same time (the
+    all-cores figure: independent copies of the sample, the oracle's
+    iteration being sequential NumPy/SciPy code).  BLAS and OpenMP pools are
+    limited to one thread before NumPy loads in each."""
+    one = _oracle_workers(seconds, 1)[0]
+    cores = os.cpu_count() or 1
+    many = _oracle_workers(seconds, cores)
+    ok = [m for m in many if m is not None]
+    if one is None or not ok:
+        out = _cpu_baseline_here(seconds)  # threads not pinned in this process
+        out["sample"] += " (in-process: BLAS threads not pinned)"
+        out["cores"] = None
+        return out
+    total = sum(m["value"] for m in ok)
+    return {"value": round(total, 5), "unit": "MDoF/s", "cores": len(ok), "kind": "oracle",
+            "single_core_value": one["value"],
+            "sample": f"oracle V-cycle + CSR apply (one FCG iteration) on the same discretisation at 8^3 cells, "
+                      f"one single-threaded copy per host core ({len(ok)} of {cores} ran), ~{seconds:.0f} s each; "
+                      f"single core alone: {one['sample']}"}
 
 
 def _cpu_baseline_here(seconds):
@@ -743,6 +901,12 @@ def main():
                     choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep", "table2"])
     ap.add_argument("--max-dofs", type=float, default=2e7, help="largest case of --mode table2")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    # workload of the kernel-only modes (default: the benchmark's 3D Q3 64^3, 6 levels)
+    ap.add_argument("--dim", type=int, default=DIM)
+    ap.add_argument("--degree", type=int, default=K)
+    ap.add_argument("--log2n", type=int, default=LOG2N)
+    ap.add_argument("--levels", type=int, default=NLEV)
+    ap.add_argument("--colour", type=int, default=-1, help="--mode smooth: one colour (default all)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -42,7 +42,9 @@
  * Tuning (read by sipg_create): SIPG_FUSED_SMOOTHING=0 in the environment
  * turns off the single cooperative launch per smoothing step on small levels
  * (the colours are then launched one by one; the results are the same);
- * SIPG_AUTOTUNE=0 skips the bind-time autotuning (sipg_tuning).
+ * SIPG_AUTOTUNE=0 skips the bind-time autotuning (sipg_tuning); SIPG_TILE=0
+ * or 1 pins the interior tile of the 3D FP32 colour pass (default or half as
+ * many patches per CTA) on every level, whatever the autotuner measured.
  */
 #ifndef SIPG_H
 #define SIPG_H
@@ -205,6 +207,13 @@ sipg_status sipg_vcycle(sipg_handle* h, int prec, const void* b, void* x, void* 
  * entry and the solution on exit.  info may be NULL.  Synchronises stream. */
 sipg_status sipg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
                        sipg_info* info, void* stream);
+/* sipg_solve from the initial guess x = 0: x is output only (its contents on
+ * entry are ignored and overwritten).  The first residual is then b itself,
+ * so the first true-residual operator apply of sipg_solve is skipped; the
+ * final true residual b - A x is still verified.  Same iterates as sipg_solve
+ * with x zeroed on entry.  Synchronises stream. */
+sipg_status sipg_solve_zero(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
+                            sipg_info* info, void* stream);
 /* Adjoint solve A^T lambda = g.  The SIPG matrix is symmetric, so this is
  * the same MG-preconditioned FCG applied to g. */
 sipg_status sipg_adjoint_solve(sipg_handle* h, const double* g, double* lambda, double rtol,

@@ -190,8 +190,12 @@ class SIPG:
         return SolveInfo(info.iterations, info.status, info.rel_residual, info.nu,
                          [hist[i] for i in range(info.history_len)])
 
-    def solve(self, b, x, rtol=1e-10, maxit=200, stream=None, history=256, allow_noconv=False):
-        return self._solve(self.lib.sipg_solve, b, x, rtol, maxit, stream, history, allow_noconv)
+    def solve(self, b, x, rtol=1e-10, maxit=200, stream=None, history=256, allow_noconv=False, zero_start=False):
+        """FCG to ||r|| <= rtol ||b||; x holds the initial guess, or with
+        zero_start=True is output only (the iteration starts from x = 0 and
+        skips the first residual apply: sipg_solve_zero)."""
+        fn = self.lib.sipg_solve_zero if zero_start else self.lib.sipg_solve
+        return self._solve(fn, b, x, rtol, maxit, stream, history, allow_noconv)
 
     def adjoint_solve(self, g, lam, rtol=1e-10, maxit=200, stream=None, history=256, allow_noconv=False):
         return self._solve(self.lib.sipg_adjoint_solve, g, lam, rtol, maxit, stream, history, allow_noconv)

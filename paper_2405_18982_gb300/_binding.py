@@ -72,6 +72,7 @@ SIGNATURES = {
     "sipg_coarse_solve": (_st, [_vp, _i, _vp, _vp, _vp]),
     "sipg_vcycle": (_st, [_vp, _i, _vp, _vp, _vp]),
     "sipg_solve": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
+    "sipg_solve_zero": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
     "sipg_adjoint_solve": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
     "sipg_solve_host": (_st, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(sipg_info), _vp]),
     "sipg_gmres_workspace_bytes": (ctypes.c_size_t, [_vp, _i]),

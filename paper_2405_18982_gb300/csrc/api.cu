@@ -9,9 +9,49 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <vector>
 
 #include "sipg_internal.cuh"
+
+cudaError_t smem_opt_in(const void* kernel, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(std::make_tuple(kernel, dev, bytes))) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert(std::make_tuple(kernel, dev, bytes));
+  return e;
+}
+
+cudaError_t smem_opt_in_occupancy(const void* kernel, int threads, int bytes, int* ctas_per_sm) {
+  cudaError_t e = smem_opt_in(kernel, bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int, int>, int> known;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(kernel, dev, threads, bytes);
+  auto it = known.find(key);
+  if (it != known.end()) {
+    *ctas_per_sm = it->second;
+    return cudaSuccess;
+  }
+  int nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, (size_t)bytes);
+  if (e != cudaSuccess) return e;
+  known[key] = nb;
+  *ctas_per_sm = nb;
+  return cudaSuccess;
+}
 
 namespace {
 
@@ -197,6 +237,7 @@ struct FcgRun {
   int it = 0, restarts = 0;
   sipg_status result = SIPG_OK;
   std::vector<double> hist;
+  bool zero_start = false;  // x = 0 on entry: the first residual is b
 };
 
 bool run_any(const sipg_handle* h, bool (*pred)(const KrylovScalars&)) {
@@ -218,8 +259,15 @@ sipg_status queue_scalars(FcgRun& r) {
 
 sipg_status launch_true_residual(FcgRun& r) {
   sipg_handle* h = r.h;
-  SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_RESIDUAL, r.b, r.x, h->kr(), r.s), "residual");
-  h->launches += 1;
+  if (r.zero_start && r.phase == FcgRun::INITIAL) {
+    // x = 0: r = b without an operator apply
+    const size_t bytes = h->lv[h->L].ndofs * h->prm.nrhs * sizeof(double);
+    SIPG_CHECK(cudaMemsetAsync(r.x, 0, bytes, r.s), "memset");
+    SIPG_CHECK(cudaMemcpyAsync(h->kr(), r.b, bytes, cudaMemcpyDeviceToDevice, r.s), "copy");
+  } else {
+    SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_RESIDUAL, r.b, r.x, h->kr(), r.s), "residual");
+    h->launches += 1;
+  }
   SIPG_CHECK(krylov_init_norms(h, r.b, h->kr(), r.s), "norms");
   return queue_scalars(r);
 }
@@ -356,9 +404,10 @@ sipg_status drive(std::vector<FcgRun>& runs) {
 }
 
 sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
-                      sipg_info* info, cudaStream_t s) {
+                      sipg_info* info, cudaStream_t s, bool zero_start = false) {
   h->rtol2 = rtol * rtol;
   std::vector<FcgRun> runs(1);
+  runs[0].zero_start = zero_start;
   runs[0].h = h;
   runs[0].b = b;
   runs[0].x = x;
@@ -683,6 +732,7 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   // colour; SIPG_AUTOTUNE=0 skips the bind-time timing of the launch paths
   if (const char* env = getenv("SIPG_FUSED_SMOOTHING")) h->fuse_small_levels = atoi(env) != 0;
   if (const char* env = getenv("SIPG_AUTOTUNE")) h->autotune = atoi(env) != 0;
+  if (const char* env = getenv("SIPG_TILE")) h->force_tile = atoi(env) == 1 ? 1 : 0;
   h->n = n;
   h->L = L;
   for (int l = 0; l <= L; ++l) {
@@ -962,6 +1012,15 @@ sipg_status sipg_solve(sipg_handle* h, const double* b, double* x, double rtol, 
   return fcg_solve(h, b, x, rtol, maxit, info, S(stream));
 }
 
+sipg_status sipg_solve_zero(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
+                            sipg_info* info, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  if (!(rtol > 0.0) || maxit < 0) return fail(h, SIPG_EINVAL, "bad rtol or maxit");
+  return fcg_solve(h, b, x, rtol, maxit, info, S(stream), true);
+}
+
 size_t sipg_gmres_workspace_bytes(const sipg_handle* h, int restart) {
   if (!h || restart < 1 || restart > SIPG_GMRES_MAX_RESTART) return 0;
   return gmres_layout(h, restart).total;
@@ -1000,8 +1059,7 @@ sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host
   SIPG_CHECK(cudaMemcpyAsync(dx, f_host, bytes, cudaMemcpyHostToDevice, s), "H2D");
   SIPG_CHECK(launch_mass(h, dx, db, s), "mass");
   h->launches += 1;
-  SIPG_CHECK(cudaMemsetAsync(dx, 0, bytes, s), "memset");
-  sipg_status r = fcg_solve(h, db, dx, rtol, maxit, info, s);
+  sipg_status r = fcg_solve(h, db, dx, rtol, maxit, info, s, true);
   if (r != SIPG_OK && r != SIPG_ENOCONV) return r;
   SIPG_CHECK(cudaMemcpyAsync(u_host, dx, bytes, cudaMemcpyDeviceToHost, s), "D2H");
   SIPG_CHECK(cudaStreamSynchronize(s), "sync");

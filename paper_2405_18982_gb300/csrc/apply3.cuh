@@ -347,18 +347,14 @@ cudaError_t launch_apply3(const sipg_handle* h, int level, int mode, const T* b,
   const LevelInfo& li = h->lv[level];
   const int N = li.N;
   if (N % 2 != 0 || (N / 2) % C::G != 0) return cudaErrorNotSupported;
-  static bool attr[3] = {false, false, false};
   const A3Ops<NN, T> op = a3_ops<NN, T>(h->hcst<T>(level));
   const long long nblk = (long long)(N / 2 / C::G) * (N / 2) * (N / 2);
   dim3 grid((unsigned)nblk, h->prm.nrhs);
   const long long nout = mode == A3_RESTRICT ? (long long)h->lv[level - 1].ndofs : (long long)li.ndofs;
   cudaError_t e = cudaSuccess;
-  auto go = [&](auto kern, int m) {
-    if (!attr[m]) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-      if (e != cudaSuccess) return;
-      attr[m] = true;
-    }
+  auto go = [&](auto kern, int) {
+    e = smem_opt_in(reinterpret_cast<const void*>(kern), (int)C::SMEM);
+    if (e != cudaSuccess) return;
     kern<<<grid, C::THREADS, C::SMEM, s>>>(op, b, x, out, N, (long long)li.ndofs, nout);
     e = cudaGetLastError();
   };

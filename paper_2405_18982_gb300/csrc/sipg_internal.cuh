@@ -117,7 +117,9 @@ struct sipg_handle {
   int tuned_path(int prec, int l) const {
     return l >= 0 && l < (int)tune_path[prec].size() ? tune_path[prec][l] : -1;
   }
+  int force_tile = -1;                       // SIPG_TILE: this interior tile on every level (tests)
   int tuned_tile(int prec, int l) const {
+    if (force_tile >= 0) return force_tile;
     return l >= 0 && l < (int)tune_tile[prec].size() ? tune_tile[prec][l] : 0;
   }
   // second stream for the boundary-patch kernel of a colour pass, forked
@@ -217,5 +219,13 @@ cudaError_t gmres_scale(sipg_handle* h, double* w, double a, long long n, cudaSt
 cudaError_t convert_d2f(const double* a, float* b, size_t n, cudaStream_t s);
 cudaError_t convert_f2d(const float* a, double* b, size_t n, cudaStream_t s);
 cudaError_t copy_or_zero(void* dst, size_t bytes, cudaStream_t s);
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per (kernel, device, bytes).  cudaFuncSetAttribute acts on the
+// current device only, so the record is kept per device; a mutex guards it
+// against concurrent first calls from several host threads.
+cudaError_t smem_opt_in(const void* kernel, int bytes);
+// smem_opt_in, then the kernel's resident CTAs per SM at that launch shape on
+// the current device (cached per kernel, device and shape).
+cudaError_t smem_opt_in_occupancy(const void* kernel, int threads, int bytes, int* ctas_per_sm);
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

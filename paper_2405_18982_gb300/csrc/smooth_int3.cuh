@@ -418,13 +418,8 @@ cudaError_t launch_int3(const sipg_handle* h, int level, int colour, const T* b,
   using C = I3<NN, T, BND, TILE>;
   const long long np = BND ? g.n_bnd : g.n_int;
   if (np <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(smooth_int3_kernel<NN, T, BND, TILE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(smooth_int3_kernel<NN, T, BND, TILE>), (int)C::SMEM);
+  if (e != cudaSuccess) return e;
   SmoothOps<C::PO, C::P, T, C::NT> ops;
   for (int t = 0; t < C::NT; ++t) make_ops<C::PO, C::P, BND, T>(h->hcst<T>(level), t, ops.t[t]);
   cudaLaunchConfig_t cfg = {};

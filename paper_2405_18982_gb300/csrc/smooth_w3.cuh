@@ -376,16 +376,10 @@ template <int NN, typename T>
 cudaError_t stepw3_dispatch(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s) {
   using F = FW3<NN, T>;
   if (F::SMEM > 227 * 1024 || h->num_sms <= 0) return cudaErrorNotSupported;
-  static int max_active = -1;
-  if (max_active < 0) {
-    cudaError_t e = cudaFuncSetAttribute(stepw3_kernel<NN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)F::SMEM);
-    if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stepw3_kernel<NN, T>, F::THREADS, F::SMEM);
-    if (e != cudaSuccess) return e;
-    max_active = nb;
-  }
+  int max_active = 0;
+  cudaError_t e0 = smem_opt_in_occupancy(reinterpret_cast<const void*>(stepw3_kernel<NN, T>), F::THREADS,
+                                         (int)F::SMEM, &max_active);
+  if (e0 != cudaSuccess) return e0;
   if (max_active <= 0) return cudaErrorNotSupported;
   const int N = h->lv[level].N;
   StepGrids sg;

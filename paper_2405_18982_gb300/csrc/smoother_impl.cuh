@@ -841,13 +841,8 @@ cudaError_t launch_part(const sipg_handle* h, int level, int colour, const T* b,
   constexpr int PPC = smooth_ppc<DIM, NN, BND, T>();
   using C = SC<DIM, NN, BND, T>;
   const size_t smem = smooth_smem_bytes<DIM, NN, BND, T>();
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(smooth_fast_kernel<DIM, NN, BND, T, PPC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(smooth_fast_kernel<DIM, NN, BND, T, PPC>), (int)smem);
+  if (e != cudaSuccess) return e;
   SmoothOps<C::PO, C::P, T, C::NT> ops;
   for (int t = 0; t < C::NT; ++t) make_ops<C::PO, C::P, BND, T>(h->hcst<T>(level), t, ops.t[t]);
   dim3 grid((unsigned)((np + PPC - 1) / PPC), h->prm.nrhs);
@@ -876,23 +871,34 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* status, uns
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = bar + 1;
-    const unsigned int gen = *vgen;
+    volatile int* vstatus = status;
     int good = 1;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
-    if (arrived == expected) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+    if (*vstatus != 0) {
+      // an earlier wait gave up: the arrival count is no longer aligned, so
+      // leave at once instead of spending another full wait
+      good = 0;
     } else {
-      long long it = 0;
-      while (*vgen == gen) {
-        if (++it > (1LL << 23)) {
-          good = 0;
-          atomicExch(status, 1);
-          break;
+      const unsigned int gen = *vgen;
+      __threadfence();
+      const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+      if (arrived == expected) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        long long it = 0;
+        while (*vgen == gen) {
+          if (*vstatus != 0) {  // another CTA gave up
+            good = 0;
+            break;
+          }
+          if (++it > (1LL << 23)) {
+            good = 0;
+            atomicExch(status, 1);
+            break;
+          }
+          __nanosleep(40);
         }
-        __nanosleep(40);
       }
     }
     __threadfence();
@@ -1047,16 +1053,10 @@ cudaError_t step_dispatch2(const sipg_handle* h, int level, int reverse, const T
   }
   using Cfg = StepCfg<DIM, NN, T>;
   if (Cfg::SMEM > 227 * 1024 || h->num_sms <= 0) return cudaErrorNotSupported;
-  static int max_active = -1;
-  if (max_active < 0) {
-    cudaError_t e = cudaFuncSetAttribute(smooth_step_kernel<DIM, NN, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, smooth_step_kernel<DIM, NN, T>, Cfg::THREADS, Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    max_active = nb;
-  }
+  int max_active = 0;
+  cudaError_t e0 = smem_opt_in_occupancy(reinterpret_cast<const void*>(smooth_step_kernel<DIM, NN, T>),
+                                         Cfg::THREADS, (int)Cfg::SMEM, &max_active);
+  if (e0 != cudaSuccess) return e0;
   if (max_active <= 0) return cudaErrorNotSupported;
   const int N = h->lv[level].N;
   StepGrids sg;

@@ -349,24 +349,15 @@ cudaError_t launch_coarse_solve(const sipg_handle* h, const T* b0, T* x0, cudaSt
   // the largest coarse problem (m^d <= 4096, m <= 64) needs at most
   // (64^2 + 2 * 4096) doubles; opt in once per instantiation
   const int max_smem = (SIPG_MAXM0 * SIPG_MAXM0 + 2 * 4096) * (int)sizeof(double);
-  static bool attr2 = false, attr3 = false;
   cudaError_t e;
   if (h->prm.dim == 2) {
-    if (!attr2) {
-      e = cudaFuncSetAttribute(coarse_solve_kernel<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               max_smem);
-      if (e != cudaSuccess) return e;
-      attr2 = true;
-    }
+    e = smem_opt_in(reinterpret_cast<const void*>(coarse_solve_kernel<2, T>), max_smem);
+    if (e != cudaSuccess) return e;
     coarse_solve_kernel<2, T><<<h->prm.nrhs, 512, smem, s>>>(h->c64(0), b0, x0, l0.N, h->n,
                                                             (long long)l0.ndofs);
   } else {
-    if (!attr3) {
-      e = cudaFuncSetAttribute(coarse_solve_kernel<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               max_smem);
-      if (e != cudaSuccess) return e;
-      attr3 = true;
-    }
+    e = smem_opt_in(reinterpret_cast<const void*>(coarse_solve_kernel<3, T>), max_smem);
+    if (e != cudaSuccess) return e;
     coarse_solve_kernel<3, T><<<h->prm.nrhs, 512, smem, s>>>(h->c64(0), b0, x0, l0.N, h->n,
                                                             (long long)l0.ndofs);
   }

@@ -1,0 +1,189 @@
+"""FP32 colour passes of the Dirichlet kernel (Algorithm 1 with the
+fast-diagonalisation local solve of Eqs. inverse2d / inverse3d), element by
+element against the FP64 oracle, at sizes where one colour spans many CTAs.
+
+Per colour pass on seeded FP32 inputs b, x0 (2D N = 128 and 3D N = 32, k =
+2..7, the consistent residual and the paper's Dirichlet-kernel residual of
+Sec. 3.1): the DoFs outside the colour's spaces V_j stay bit-identical, and
+on sampled patches (the first and last patch of the launch, every kind of
+domain-boundary patch, random interior ones) x - x0 equals the oracle's dense
+patch solve A_j^{-1} r_j to 1e-4 relative (FP32 fast diagonalisation of patch
+matrices with condition numbers up to ~1e3).  Each case runs with the
+launch path pinned (no autotuning, colour-by-colour launches) on both
+interior tiles of the 3D kernel, and with the autotuned choice.
+
+Also: the two largest distinct members of the ragged 2D batch (2^9 x 2^9
+cells, k = 5, 6) through the batch's member handles, and the multi-RHS case
+(3D Q4 on 32^3 cells, 32 right-hand sides) -- sampled apply rows and patch
+solves of a few columns, and every column's solution against the oracle's
+exact global fast-diagonalisation solve."""
+import numpy as np
+import pytest
+
+from gpu_helpers import dev, gpu_available, host
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+from oracle.assembly import block_apply, element_blocks  # noqa: E402
+from oracle.direct import GlobalFD  # noqa: E402
+from paper_2405_18982_gb300 import (SIPG, SIPG_FP32, SIPG_SMOOTHER_CONSISTENT, SIPG_SMOOTHER_PAPER,  # noqa: E402
+                                    Params, SIPGBatch, inputs)
+from patch_sampling import PatchOracle, colour_touch_mask, sample_vertices  # noqa: E402
+
+CASES = [(2, k, 7) for k in range(2, 8)] + [(3, k, 5) for k in range(2, 8)]
+IDS = [f"d{d}k{k}N{1 << l}" for d, k, l in CASES]
+PATHS = {"pinned": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "0"},
+         "pinned_half_tile": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "1"},
+         "tuned": {}}
+VARIANTS = {"consistent": SIPG_SMOOTHER_CONSISTENT, "paper": SIPG_SMOOTHER_PAPER}
+TOL = 1e-4
+
+
+def _f32(a):
+    return a.astype(np.float32).astype(np.float64)
+
+
+_ORACLES = {}
+
+
+def patch_oracle(dim, k, N, variant):
+    """One PatchOracle per mesh and residual (its factors are reused by the
+    three launch paths)."""
+    key = (dim, k, N, variant)
+    if key not in _ORACLES:
+        _ORACLES.clear()
+        _ORACLES[key] = PatchOracle(dim, k, N, variant)
+    return _ORACLES[key]
+
+
+def check_colour_passes(s, level, dim, k, N, variant, seed, samples, colours=None):
+    """Runs every colour pass of `level` on the handle from seeded FP32
+    inputs and checks it against the oracle; returns the worst relative
+    error over the sampled patches."""
+    import torch
+    nd = s.ndofs(level)
+    b = _f32(inputs.normal(seed, nd))
+    x0 = _f32(inputs.normal(seed + 1, nd))
+    bd = dev(b, torch.float32).view(1, -1)
+    po = patch_oracle(dim, k, N, variant)
+    worst = 0.0
+    for c in (range(2 ** dim) if colours is None else colours):
+        xd = dev(x0, torch.float32).view(1, -1)
+        s.smooth_colour(level, c, bd, xd)
+        x1 = host(xd).ravel()
+        touch = colour_touch_mask(dim, k, N, c)
+        assert np.array_equal(x1[~touch], x0[~touch]), f"colour {c} wrote outside its patch spaces"
+        du = x1 - x0
+        for v in sample_vertices(dim, N, c, seed + 10 + c, samples):
+            idx, u = po.update(v, b, x0)
+            err = np.abs(du[idx] - u).max() / np.abs(u).max()
+            worst = max(worst, err)
+            assert err < TOL, (c, v, err)
+    return worst
+
+
+@pytest.mark.parametrize("path", list(PATHS), ids=list(PATHS))
+@pytest.mark.parametrize("variant", list(VARIANTS), ids=list(VARIANTS))
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_smooth_colour_fp32(case, variant, path, monkeypatch):
+    dim, k, l2 = case
+    if path == "pinned_half_tile" and dim == 2:
+        pytest.skip("the 2D colour pass has one tile")
+    for key, val in PATHS[path].items():
+        monkeypatch.setenv(key, val)
+    N = 1 << l2
+    s = SIPG(Params(dim=dim, degree=k, log2_cells=l2, n_levels=l2, vcycle_precision=SIPG_FP32,
+                    smoother=VARIANTS[variant]))
+    samples = 10 if (dim == 3 and k >= 6) else 16
+    worst = check_colour_passes(s, l2 - 1, dim, k, N, variant, 4000 + 10 * k + dim, samples)
+    print(f"{case} {variant} {path}: worst sampled-patch error {worst:.2e}")
+    s.close()
+
+
+def test_ragged_largest_members_colour_passes():
+    # the two largest distinct shapes of the 64-problem batch (seed 4): 2D,
+    # 512 x 512 cells, k = 6 and k = 5, driven through the batch's member
+    # handles on the finest level
+    shapes = sorted(set(inputs.ragged_problems(4)), key=lambda t: (1 << t[0]) ** 2 * (t[1] + 1) ** 2)[-2:]
+    bt = SIPGBatch([Params(dim=2, degree=k, log2_cells=L, n_levels=L, vcycle_precision=SIPG_FP32, use_graphs=1)
+                    for L, k in shapes])
+    for (L, k), m in zip(shapes, bt.members):
+        worst = check_colour_passes(m, L - 1, 2, k, 1 << L, "consistent", 4100 + k, 12)
+        print(f"ragged member L={L} k={k}: worst sampled-patch error {worst:.2e}")
+    bt.close()
+
+
+@pytest.fixture(scope="module")
+def multirhs():
+    import torch
+    dim, k, l2, nrhs = 3, 4, 5, 32
+    s = SIPG(Params(dim=dim, degree=k, log2_cells=l2, n_levels=l2, vcycle_precision=SIPG_FP32, nrhs=nrhs,
+                    use_graphs=1))
+    nd = s.ndofs()
+    B = inputs.normal_columns(list(range(100, 100 + nrhs)), nd)
+    X = torch.zeros(nrhs, nd, dtype=torch.float64, device="cuda")
+    # 1e-11: near the FP64 residual floor, so that the solution error is the
+    # solver's and not the conditioning's (A's condition number ~ k^4 / h^2)
+    info = s.solve(dev(B), X, rtol=1e-11, maxit=100, allow_noconv=True)
+    return s, B, host(X), info
+
+
+def test_multirhs_solutions_match_direct(multirhs):
+    s, B, X, info = multirhs
+    assert info.rel_residual <= 2e-11
+    fd = GlobalFD(3, 4, 32)
+    for c in range(B.shape[0]):
+        u = fd.solve(B[c])
+        err = np.linalg.norm(X[c] - u) / np.linalg.norm(u)
+        assert err < 1e-8, (c, err)
+
+
+def test_multirhs_apply_and_colour_pass_columns(multirhs):
+    import torch
+    s, _, _, _ = multirhs
+    dim, k, N, nrhs = 3, 4, 32, 32
+    n = k + 1
+    nd = s.ndofs()
+    blocks = element_blocks(dim, k, N)
+    cols = [0, 13, 31]
+
+    def columns(seed, fn):
+        # the sampled columns seeded, the others zero (every column is still
+        # processed by the kernels)
+        out = np.zeros((nrhs, nd))
+        for c in cols:
+            out[c] = _f32(fn(seed + c, nd))
+        return out
+
+    Xin = columns(4200, inputs.uniform)
+    Y = torch.zeros(nrhs, nd, dtype=torch.float32, device="cuda")
+    s.apply(s.params.n_levels - 1, dev(Xin, torch.float32), Y)
+    Yh = host(Y)
+    rng = np.random.default_rng(4201)
+    cells = np.sort(rng.choice(N ** dim, size=300, replace=False))
+    absb = {key: (np.abs(v) if not isinstance(v, list) else [[np.abs(q) for q in r] for r in v])
+            for key, v in blocks.items()}
+    for c in cols:
+        ref = block_apply(dim, k, N, blocks, Xin[c], cells)
+        scale = block_apply(dim, k, N, absb, np.abs(Xin[c]), cells).max()
+        got = Yh[c].reshape(-1, n ** dim)[cells]
+        assert np.abs(got - ref).max() < 64 * 6e-8 * scale, c
+    # one colour pass on all 32 columns at once; sampled patches of three columns
+    Bc = columns(4300, inputs.normal)
+    X0 = columns(4400, inputs.normal)
+    po = PatchOracle(dim, k, N)
+    for colour in (0, 5):
+        Xd = dev(X0, torch.float32)
+        s.smooth_colour(s.params.n_levels - 1, colour, dev(Bc, torch.float32), Xd)
+        X1 = host(Xd)
+        touch = colour_touch_mask(dim, k, N, colour)
+        for c in range(nrhs):
+            if c not in cols:
+                assert not X1[c].any()          # zero b and x stay zero
+                continue
+            assert np.array_equal(X1[c][~touch], X0[c][~touch])
+            du = X1[c] - X0[c]
+            for v in sample_vertices(dim, N, colour, 4500 + c, 8):
+                idx, u = po.update(v, Bc[c], X0[c])
+                assert np.abs(du[idx] - u).max() / np.abs(u).max() < TOL, (colour, c, v)

@@ -282,13 +282,15 @@ def test_multi_rhs_and_graphs(monkeypatch):
         F[2] *= 1e-3                     # columns of very different scale
         B = np.stack([rhs_from_nodal(dim, k, N, f) for f in F])
         X = dev(np.zeros_like(B))
-        info = s.solve(dev(B), X, rtol=1e-10, maxit=100)
+        # every column to rtol 1e-12 (as the single-RHS solves), then the
+        # mixed solution's 1e-8
+        info = s.solve(dev(B), X, rtol=1e-12, maxit=100)
         got = host(X)
         fd = GlobalFD(dim, k, N)
         for c in range(3):
             u = fd.solve(B[c])
-            assert rel_inf(got[c], u) < 1e-7
-        assert info.rel_residual <= 1e-10
+            assert rel_inf(got[c], u) < 1e-8
+        assert info.rel_residual <= 1e-12
         if graphs == 0:
             ref = got
         else:
