@@ -511,7 +511,8 @@ def run_kernel_only(args):
     import paper_2405_18982_gb300 as pkg
     from paper_2405_18982_gb300 import SIPG, SIPG_FP32, SIPG_FP64, Params, inputs
     pkg.load(pkg.build())
-    prec = SIPG_FP64 if args.precision == "fp64" else SIPG_FP32
+    from paper_2405_18982_gb300 import SIPG_TF32
+    prec = {"fp64": SIPG_FP64, "fp32": SIPG_FP32, "tf32": SIPG_TF32}[args.precision]
     dt = torch.float64 if prec == SIPG_FP64 else torch.float32
     dim, k, l2 = args.dim, args.degree, args.log2n
     nlev = args.levels or l2
@@ -900,7 +901,7 @@ def main():
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep", "table2"])
     ap.add_argument("--max-dofs", type=float, default=2e7, help="largest case of --mode table2")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
     # workload of the kernel-only modes (default: the benchmark's 3D Q3 64^3, 6 levels)
     ap.add_argument("--dim", type=int, default=DIM)
     ap.add_argument("--degree", type=int, default=K)

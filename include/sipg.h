@@ -70,10 +70,15 @@ typedef enum {
 
 /* Arithmetic of the V-cycle (operator apply, smoother, transfer); the outer
  * Krylov solver, its residual, dot products and updates, the 1D eigenpair
- * setup and the coarse solve are always FP64. */
+ * setup and the coarse solve are always FP64.  SIPG_TF32 (params only) is
+ * the FP32 V-cycle whose interior 3D colour passes at degree 7 run the six
+ * eigenvector sweeps of the fast-diagonalisation local solve (Eq. inverse3d)
+ * on the tensor cores with TF32 operands and FP32 accumulation; everything
+ * else, and the vector type of every call (prec arguments), is FP32. */
 typedef enum {
   SIPG_FP64 = 0,
-  SIPG_FP32 = 1
+  SIPG_FP32 = 1,
+  SIPG_TF32 = 2
 } sipg_precision;
 
 /* Local residual of the Dirichlet-kernel patch solver (Sec. 3.1). */
@@ -304,6 +309,14 @@ sipg_status sipg_batch_solve(sipg_batch* b, const double* const* bvecs, double* 
 sipg_status sipg_dot_noalloc(sipg_handle* h, const double* a, const double* b, double* out,
                              void* stream);
 
+/* Self-test of the tensor-core path (no counterpart in the paper): one CTA
+ * computes D = A B^T with A 256 x 16 and B 16 x 16 (row-major FP32 device
+ * arrays, rounded to TF32, FP32 accumulation) through the same operand
+ * layouts, MMA issue, completion wait and tensor-memory loads as the TF32
+ * colour pass, and writes D (256 x 16, row-major).  Needs a bound workspace
+ * (for the status word); SIPG_ETIMEOUT if the bounded completion wait ran
+ * out.  Synchronises stream. */
+sipg_status sipg_selftest_mma_tf32(sipg_handle* h, const float* a, const float* b, float* d, void* stream);
 /* Self test of the bounded device-side waits (fused smoothing steps separate
  * their colours by a grid barrier whose waits give up after about half a
  * second, set a status word and return, so a stuck barrier is reported as

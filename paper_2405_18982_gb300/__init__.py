@@ -12,10 +12,10 @@ import ctypes
 from dataclasses import dataclass
 
 from . import _binding as B
-from ._binding import (SIPG_FP32, SIPG_FP64, SIPG_SMOOTHER_CLAMPED, SIPG_SMOOTHER_CONSISTENT,
+from ._binding import (SIPG_FP32, SIPG_FP64, SIPG_TF32, SIPG_SMOOTHER_CLAMPED, SIPG_SMOOTHER_CONSISTENT,
                        SIPG_SMOOTHER_FULL, SIPG_SMOOTHER_PAPER, SipgError, load)
 
-__all__ = ["Params", "SIPG", "SIPGBatch", "SipgError", "SIPG_FP64", "SIPG_FP32",
+__all__ = ["Params", "SIPG", "SIPGBatch", "SipgError", "SIPG_FP64", "SIPG_FP32", "SIPG_TF32",
            "SIPG_SMOOTHER_CONSISTENT", "SIPG_SMOOTHER_PAPER", "SIPG_SMOOTHER_FULL",
            "SIPG_SMOOTHER_CLAMPED", "load", "build"]
 
@@ -236,6 +236,11 @@ class SIPG:
         self._check(st)
         return SolveInfo(info.iterations, info.status, info.rel_residual, info.nu,
                          [hist[i] for i in range(info.history_len)])
+
+    def selftest_mma_tf32(self, a, b, d, stream=None):
+        """Tensor-core self test (sipg_selftest_mma_tf32): d = a b^T for a
+        (256, 16) and b (16, 16) float32 CUDA tensors, TF32 operands."""
+        return self._check(self.lib.sipg_selftest_mma_tf32(self.h, _ptr(a), _ptr(b), _ptr(d), self._stream(stream)))
 
     def tuning(self, level, precision=None):
         """(path, tile) chosen by the bind-time autotuner for `level`."""

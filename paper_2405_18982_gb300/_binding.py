@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM_WORKSPACE", -3: "ECUDA", -4: 
 
 SIPG_FP64 = 0
 SIPG_FP32 = 1
+SIPG_TF32 = 2
 SIPG_SMOOTHER_CONSISTENT = 0
 SIPG_SMOOTHER_PAPER = 1
 SIPG_SMOOTHER_FULL = 2
@@ -81,6 +82,7 @@ SIGNATURES = {
     "sipg_dot": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_dot_noalloc": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_selftest_barrier": (_st, [_vp, _i, _vp]),
+    "sipg_selftest_mma_tf32": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_get_constants": (_st, [_vp, _i, _i, _i, _vp, _i, ctypes.POINTER(_i), _vp]),
     "sipg_tuning": (_st, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "sipg_batch_create": (_st, [ctypes.POINTER(sipg_params), _i, ctypes.POINTER(_vp)]),

@@ -710,7 +710,8 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   if (p->n_levels < 1 || p->n_levels > p->log2_cells) return SIPG_EINVAL;
   if (!(p->kappa > 0.0) || !isfinite(p->kappa)) return SIPG_EINVAL;
   if (!(p->penalty_factor > 0.0) || !isfinite(p->penalty_factor)) return SIPG_EINVAL;
-  if (p->vcycle_precision != SIPG_FP64 && p->vcycle_precision != SIPG_FP32) return SIPG_EINVAL;
+  if (p->vcycle_precision != SIPG_FP64 && p->vcycle_precision != SIPG_FP32 && p->vcycle_precision != SIPG_TF32)
+    return SIPG_EINVAL;
   if (p->smoother != SIPG_SMOOTHER_CONSISTENT && p->smoother != SIPG_SMOOTHER_PAPER &&
       p->smoother != SIPG_SMOOTHER_FULL && p->smoother != SIPG_SMOOTHER_CLAMPED)
     return SIPG_EINVAL;
@@ -728,6 +729,10 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
 
   sipg_handle* h = new sipg_handle();
   h->prm = *p;
+  // TF32: the FP32 V-cycle with tensor-core local solves where a kernel for
+  // them exists; every other code path treats the handle as FP32
+  h->tf32 = p->vcycle_precision == SIPG_TF32;
+  if (h->tf32) h->prm.vcycle_precision = SIPG_FP32;
   // tuning knobs: SIPG_FUSED_SMOOTHING=0 launches small levels colour by
   // colour; SIPG_AUTOTUNE=0 skips the bind-time timing of the launch paths
   if (const char* env = getenv("SIPG_FUSED_SMOOTHING")) h->fuse_small_levels = atoi(env) != 0;
@@ -1093,6 +1098,25 @@ sipg_status sipg_selftest_barrier(sipg_handle* h, int extra, void* stream) {
   return SIPG_OK;
 }
 
+sipg_status sipg_selftest_mma_tf32(sipg_handle* h, const float* a, const float* b, float* d, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (!a || !b || !d) return fail(h, SIPG_EINVAL, "null pointer");
+  cudaStream_t s = S(stream);
+  SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+  SIPG_CHECK(launch_tc_selftest(h, a, b, d, s), "tensor-core self test");
+  h->launches += 1;
+  int status = 0;
+  SIPG_CHECK(cudaMemcpyAsync(&status, h->ws + h->off_sync + 2 * sizeof(unsigned int), sizeof(int),
+                             cudaMemcpyDeviceToHost, s),
+             "status D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  SIPG_CHECK(cudaMemsetAsync(h->ws + h->off_sync, 0, 256, s), "memset");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  if (status != 0) return fail(h, SIPG_ETIMEOUT, "tensor-core completion wait timed out (self test)");
+  return SIPG_OK;
+}
+
 sipg_status sipg_get_constants(sipg_handle* h, int level, int which, int type, double* host_out, int cap,
                                int* count, void* stream) {
   sipg_status st = need_bound(h);
@@ -1156,8 +1180,9 @@ sipg_status sipg_get_constants(sipg_handle* h, int level, int which, int type, d
 
 sipg_status sipg_tuning(const sipg_handle* h, int level, int precision, int* path, int* tile) {
   if (!h || !path || !tile) return SIPG_EINVAL;
-  if (level < 0 || level > h->L || (precision != SIPG_FP64 && precision != SIPG_FP32)) return SIPG_EINVAL;
-  const int pi = precision == SIPG_FP32 ? 1 : 0;
+  if (level < 0 || level > h->L || (precision != SIPG_FP64 && precision != SIPG_FP32 && precision != SIPG_TF32))
+    return SIPG_EINVAL;
+  const int pi = precision != SIPG_FP64 ? 1 : 0;
   *path = h->tuned_path(pi, level);
   *tile = h->tuned_tile(pi, level);
   return SIPG_OK;

@@ -117,6 +117,7 @@ struct sipg_handle {
   int tuned_path(int prec, int l) const {
     return l >= 0 && l < (int)tune_path[prec].size() ? tune_path[prec][l] : -1;
   }
+  bool tf32 = false;                         // tensor-core (TF32) local solves where available
   int force_tile = -1;                       // SIPG_TILE: this interior tile on every level (tests)
   int tuned_tile(int prec, int l) const {
     if (force_tile >= 0) return force_tile;
@@ -224,6 +225,11 @@ cudaError_t copy_or_zero(void* dst, size_t bytes, cudaStream_t s);
 // current device only, so the record is kept per device; a mutex guards it
 // against concurrent first calls from several host threads.
 cudaError_t smem_opt_in(const void* kernel, int bytes);
+// Interior patches of a 3D FP32 colour pass with the fast-diagonalisation
+// sweeps on the tensor cores (TF32); cudaErrorNotSupported where that kernel
+// does not apply (the caller then launches the FP32 kernel).
+cudaError_t launch_tc3(const sipg_handle* h, int level, int colour, const float* b, float* x, cudaStream_t s);
+cudaError_t launch_tc_selftest(const sipg_handle* h, const float* A, const float* B, float* D, cudaStream_t s);
 // smem_opt_in, then the kernel's resident CTAs per SM at that launch shape on
 // the current device (cached per kernel, device and shape).
 cudaError_t smem_opt_in_occupancy(const void* kernel, int threads, int bytes, int* ctas_per_sm);

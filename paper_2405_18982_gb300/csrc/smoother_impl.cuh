@@ -920,6 +920,13 @@ cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T*
         (reinterpret_cast<uintptr_t>(x) % 16) == 0)
       return launch_int2<NN, T, BND>(h, level, colour, b, x, g, s);
   }
+  if constexpr (DIM == 3 && sizeof(T) == 4 && !BND) {
+    if (h->tf32) {
+      const cudaError_t e = launch_tc3(h, level, colour, reinterpret_cast<const float*>(b),
+                                       reinterpret_cast<float*>(x), s);
+      if (e != cudaErrorNotSupported) return e;
+    }
+  }
   if constexpr (DIM == 3 && sizeof(T) == 4) {
     if (use_int3<DIM, T>(g, b, x)) {
       if constexpr (!BND)
