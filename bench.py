@@ -254,6 +254,67 @@ def whole_job_mdofs(dist, device, ndofs, vcycles, seconds):
     return ndofs * total / t_max / 1e6, t_max
 
 
+C3 = (3, 7, 5, 5)   # dim, k, log2 N, levels: Q7 on 32^3 cells (16.8M DoFs)
+C3_SEED = 3
+
+
+def c3_record(torch, dev, reps=3):
+    """3D Q7 on 32^3 cells, f ~ N(0,1) per DoF (seed 3), b = M f: FP64 outer
+    flexible CG to 1e-10 preconditioned by the FP32 V-cycle and by the TF32
+    one (tensor-core fast-diagonalisation sweeps in the interior colour
+    passes), each solution's error against the FP64-V-cycle solve, and the
+    finest interior colour pass of each (colour 0, CUDA events)."""
+    from paper_2405_18982_gb300 import SIPG, SIPG_FP32, SIPG_FP64, SIPG_TF32, Params, inputs
+    dim, k, l2, nl = C3
+    out = {"workload": "3D SIPG Poisson, 32^3 cells, Q7 (16.8M DoFs), 5 levels, f ~ N(0,1) seed 3, "
+                       "FP64 flexible CG to 1e-10"}
+    sol = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    b = None
+    for tag, prec in (("fp64", SIPG_FP64), ("fp32", SIPG_FP32), ("tf32", SIPG_TF32)):
+        s = SIPG(Params(dim=dim, degree=k, log2_cells=l2, n_levels=nl, vcycle_precision=prec, use_graphs=1),
+                 device=dev)
+        if b is None:
+            f = torch.from_numpy(inputs.normal(C3_SEED, s.ndofs())).to(dev).view(1, -1)
+            b = torch.zeros_like(f)
+            s.rhs(f, b)
+        x = torch.zeros_like(b)
+        s.solve(b, x, rtol=1e-10, maxit=100, zero_start=True)   # warm-up (graph capture)
+        torch.cuda.synchronize()
+        n_rep = 1 if prec == SIPG_FP64 else reps
+        e0.record(stream)
+        for _ in range(n_rep):
+            info = s.solve(b, x, rtol=1e-10, maxit=100, zero_start=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / n_rep
+        rec = {"time_to_1e-10_s": round(t, 5), "iterations": info.iterations, "rel_residual": info.rel_residual,
+               "mdofs_per_vcycle": round(s.ndofs() * info.iterations / t / 1e6, 1)}
+        if prec != SIPG_FP64:
+            bf = b.float()
+            xf = torch.zeros_like(bf)
+            L = nl - 1
+            for _ in range(3):
+                s.smooth_colour(L, 0, bf, xf)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                s.smooth_colour(L, 0, bf, xf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rec["colour_pass_us"] = round(e0.elapsed_time(e1) / 10 * 1e3, 2)
+        sol[tag] = x
+        out[tag] = rec
+        s.close()
+        del s
+    for tag in ("fp32", "tf32"):
+        out[tag]["solution_rel_l2_vs_fp64"] = float(((sol[tag] - sol["fp64"]).norm() / sol["fp64"].norm()).item())
+    del sol
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -451,6 +512,9 @@ def run_ours(args):
                       "time with the counts of the roofline objects (smoothing step: interior-patch model for "
                       "every patch of the 2^d colours)"}
 
+    # ---- C3: the degree-7 configuration with the FP32 and the TF32 V-cycle
+    c3 = c3_record(torch, dev) if not args.no_c3 else None
+
     # ---- end to end through the public host-buffer call
     fh = f.detach().cpu().pin_memory()
     uh = torch.zeros_like(fh).pin_memory()
@@ -489,6 +553,7 @@ def run_ours(args):
             "roofline": roof,
             "roofline_fp64_apply": roof_apply,
             "per_op": per_op,
+            "c3_q7": c3,
             "e2e": {"value": round(e2e_value, 2), "unit": "MDoF/s", "h2d_bytes_per_step": n * 8,
                     "d2h_bytes_per_step": n * 8,
                     "note": "sipg_solve_host: pinned f in, b = M f, solve from 0, u out"},
@@ -897,9 +962,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="skip the degree-7 FP32 / TF32 record")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep", "table2"])
+                    choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep", "table2",
+                             "c3"])
     ap.add_argument("--max-dofs", type=float, default=2e7, help="largest case of --mode table2")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32"])
     # workload of the kernel-only modes (default: the benchmark's 3D Q3 64^3, 6 levels)
@@ -917,6 +984,11 @@ def main():
         run_sweep(args)
     elif args.mode == "table2":
         run_table2(args)
+    elif args.mode == "c3":
+        import torch
+        import paper_2405_18982_gb300 as pkg
+        pkg.load(pkg.build())
+        print(json.dumps({"mode": "c3", **c3_record(torch, torch.device("cuda", 0))}))
     elif args.mode != "solve":
         run_kernel_only(args)
     else:

@@ -199,22 +199,23 @@ __global__ void __launch_bounds__(256, 3)
     const int cs1 = N * ND, cs2 = N * N * ND;
 
     // ---------------------------------------------------------- x sweep
-    // lines t < P^2: (a1, a2) = (t / P, t % P); then 4P halo lines (slot, j)
+    // lines t < P^2: (a1, a2) = (t / P, t % P); then 4P halo lines (slot, j):
+    // slot 0/1 = y faces below/above (j = a2), 2/3 = z faces (j = a1).  All
+    // of a thread's loads are issued before any line is contracted.
     {
       constexpr int L1 = P * P + 4 * P;
       constexpr int R1 = (L1 + NT - 1) / NT;
+      float vin[R1][P], hl[R1][2];
 #pragma unroll
       for (int q = 0; q < R1; ++q) {
         const int t = tid + q * NT;
-        if (t >= L1) continue;
-        float vin[P], h0 = 0.f, h1 = 0.f;
         int off = 0;
-        bool ld = true;
-        const bool main = t < P * P;
+        const bool act = t < L1, main = t < P * P;
+        bool ld = main;
         if (main) {
           const int a2 = t % P, a1 = t / P;
           off = (a1 / NN) * cs1 + (a2 / NN) * cs2 + (a1 % NN) * NN + (a2 % NN) * NN * NN;
-        } else {
+        } else if (act) {
           const int hh = t - P * P, slot = hh / P, j = hh % P;
           if (slot < 2) {
             off = (slot ? 2 : -1) * cs1 + (slot ? 0 : (NN - 1) * NN) + (j / NN) * cs2 + (j % NN) * NN * NN;
@@ -224,23 +225,27 @@ __global__ void __launch_bounds__(256, 3)
           ld = consistent != 0;
         }
         if (ld) {
-          i3_ldrun<NN, VW, float, true>(xb + off, &vin[0]);
-          i3_ldrun<NN, VW, float, true>(xb + off + ND, &vin[NN]);
+          i3_ldrun<NN, VW, float, true>(xb + off, &vin[q][0]);
+          i3_ldrun<NN, VW, float, true>(xb + off + ND, &vin[q][NN]);
         } else {
 #pragma unroll
-          for (int c = 0; c < P; ++c) vin[c] = 0.f;
+          for (int c = 0; c < P; ++c) vin[q][c] = 0.f;
         }
-        if (main && consistent) {
-          h0 = __ldg(xb + off - ND + (NN - 1));
-          h1 = __ldg(xb + off + 2 * ND);
-        }
+        hl[q][0] = (main && consistent) ? __ldg(xb + off - ND + (NN - 1)) : 0.f;
+        hl[q][1] = (main && consistent) ? __ldg(xb + off + 2 * ND) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < R1; ++q) {
+        const int t = tid + q * NT;
+        if (t >= L1) continue;
+        const bool main = t < P * P;
         const int dst = main ? SA1 * (t / P) + PO * (t % P) : (2 * P + (t - P * P) / P) * SA1 + PO * ((t - P * P) % P);
         float oa[PO];
-        mass_rows2<PO, P, NN, OFF, false>(op, vin, oa);
+        mass_rows2<PO, P, NN, OFF, false>(op, vin[q], oa);
         i3_st_pairs<PO>(RA + dst, oa);
         if (main) {
           float ob[PO];
-          sipg_rows2<PO, P, NN, OFF>(op, vin, h0, h1, ob);
+          sipg_rows2<PO, P, NN, OFF>(op, vin[q], hl[q][0], hl[q][1], ob);
           i3_st_pairs<PO>(RA + P * SA1 + dst, ob);
         }
       }
@@ -315,6 +320,12 @@ __global__ void __launch_bounds__(256, 3)
     }
 
     // -------------------------------- fast diagonalisation on the tensor cores
+    // x on the line's V_j rows, read now so that the loads overlap the
+    // tensor-core sweeps
+    float* gx = x + (xb - x) + goff;
+    float xo[PO];
+#pragma unroll
+    for (int r2 = 0; r2 < PO; ++r2) xo[r2] = own ? gx[((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN] : 0.f;
     // (each sweep's MMA has completed before its outputs are read, so the
     // operand can be rewritten at once; ok is the same in every thread)
     float w[16];
@@ -329,9 +340,11 @@ __global__ void __launch_bounds__(256, 3)
     }
     if (ok) {
       // Lambda^{-1}: line (k1, k2) = (a, bb), k0 = j
+      // (approximate reciprocal, 2 ulp: far below the TF32 rounding of the
+      // operands this scaling feeds)
       const float lyz = own ? op.lam[a] + op.lam[bb] : 1.f;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) w[j] = (own && j < PO) ? w[j] / (op.lam[j < PO ? j : 0] + lyz) : 0.f;
+      for (int j = 0; j < 16; ++j) w[j] = (own && j < PO) ? __fdividef(w[j], op.lam[j < PO ? j : 0] + lyz) : 0.f;
       tc3_store_row<NN>(Aop, tid, w, own);  // row (k1, k2), index k0
       ok = tc3_sweep<NN>(tmem, a_s, bs_s, mbar, parity, w);  // S_x: (k1, k2) -> r0
     }
@@ -349,12 +362,8 @@ __global__ void __launch_bounds__(256, 3)
     }
     // x[V_j] += u on line (r0, r1)
     if (own) {
-      float* gx = x + (xb - x) + goff;
 #pragma unroll
-      for (int r2 = 0; r2 < PO; ++r2) {
-        float* p = gx + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN;
-        *p = *p + w[r2];
-      }
+      for (int r2 = 0; r2 < PO; ++r2) gx[((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN] = xo[r2] + w[r2];
     }
     __syncthreads();  // RA / operand A and RB are rewritten by the next patch
   }
