@@ -581,7 +581,11 @@ def run_kernel_only(args):
     dt = torch.float64 if prec == SIPG_FP64 else torch.float32
     dim, k, l2 = args.dim, args.degree, args.log2n
     nlev = args.levels or l2
-    s = SIPG(Params(dim=dim, degree=k, log2_cells=l2, n_levels=nlev, vcycle_precision=prec))
+    from paper_2405_18982_gb300 import (SIPG_SMOOTHER_CLAMPED, SIPG_SMOOTHER_CONSISTENT, SIPG_SMOOTHER_FULL,
+                                        SIPG_SMOOTHER_PAPER)
+    sm = {"consistent": SIPG_SMOOTHER_CONSISTENT, "paper": SIPG_SMOOTHER_PAPER, "full": SIPG_SMOOTHER_FULL,
+          "clamped": SIPG_SMOOTHER_CLAMPED}[args.smoother]
+    s = SIPG(Params(dim=dim, degree=k, log2_cells=l2, n_levels=nlev, vcycle_precision=prec, smoother=sm))
     n = s.ndofs()
     b = torch.from_numpy(inputs.uniform(NOISE_SEED, n)).to("cuda").view(1, n).to(dt)
     x = torch.zeros_like(b)
@@ -635,7 +639,7 @@ def run_kernel_only(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"mode": args.mode, "precision": args.precision, "dim": dim, "degree": k,
+    print(json.dumps({"mode": args.mode, "precision": args.precision, "smoother": args.smoother, "dim": dim, "degree": k,
                       "cells_per_dir": 1 << l2, "levels": nlev, "dofs": n, "colour": args.colour,
                       "ms_per_rep": round(ms, 4)}))
 
@@ -975,6 +979,7 @@ def main():
     ap.add_argument("--log2n", type=int, default=LOG2N)
     ap.add_argument("--levels", type=int, default=NLEV)
     ap.add_argument("--colour", type=int, default=-1, help="--mode smooth: one colour (default all)")
+    ap.add_argument("--smoother", default="consistent", choices=["consistent", "paper", "full", "clamped"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -4,4 +4,6 @@
 #include "smoother_impl.cuh"
 
 SIPG_SMOOTH_INST(3, float, 5)
+SIPG_CLAMPED_INST(5)
 SIPG_SMOOTH_INST(3, float, 6)
+SIPG_CLAMPED_INST(6)

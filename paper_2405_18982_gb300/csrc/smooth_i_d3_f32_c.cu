@@ -4,4 +4,6 @@
 #include "smoother_impl.cuh"
 
 SIPG_SMOOTH_INST(3, float, 7)
+SIPG_CLAMPED_INST(7)
 SIPG_SMOOTH_INST(3, float, 8)
+SIPG_CLAMPED_INST(8)

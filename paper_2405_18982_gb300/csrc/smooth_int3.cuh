@@ -443,3 +443,138 @@ bool use_int3(const PatchGrid& g, const void* b, const void* x) {
   return DIM == 3 && sizeof(T) == 4 && g.n_int < (1LL << 31) && (reinterpret_cast<uintptr_t>(b) % 16) == 0 &&
          (reinterpret_cast<uintptr_t>(x) % 16) == 0;
 }
+
+// ---------------------------------------------------------------- clamped
+// The clamped kernel (Sec. 3.1): V_j = patch functions with v = d_n v = 0 on
+// the patch boundary inside the domain.  Every face term of the patch
+// boundary vanishes for such test functions, so the local residual
+// B^T R_D (b - A x) equals B^T (R_D b - A_D R_D x) with A_D the principal
+// block of A on the 2^d patch cells: no halo, no coupling to other patches.
+// One fused pass per colour therefore runs the register-direct kernel in its
+// boundary layout (all P = 2n patch nodes per direction as rows) over every
+// patch of the colour, with per direction type t the operators
+//   rows of A_D: the full 2n x 2n patch block of the 1D SIPG matrix (own cell
+//   blocks with their face terms, rank-two couplings across the vertex),
+//   rows of M: the block-diagonal cell mass (diagonal plus rank one),
+//   S = B S_m (P x m, zero columns beyond m), Lambda (1 beyond m): the
+//   eigenpairs of the projected 1D patch matrices B^T L_D B, B^T M_D B,
+// so that u = (S (x) S (x) S) Lambda^{-1} (S (x) S (x) S)^T r_D is
+// B (B^T A_D B)^{-1} B^T r_D, added to x on the patch cells (zero on the
+// patch-end nodes).  Same-colour patches tile disjoint cells and read no
+// other patch's cells: the pass is race-free and equals the sequential one.
+template <int NN, typename T>
+void make_ops_clamped(const LevelConst<T>& lc, int t, Ops1D<2 * NN, 2 * NN, T>& op) {
+  constexpr int P = 2 * NN, k = NN - 1;
+  const int tl = (t & 1) ? 1 : 0, tr = (t & 2) ? 2 : 0;
+  for (int a = 0; a < P; ++a) {
+    const int oa = a / NN, ia = a % NN;
+    for (int c = 0; c < P; ++c) {
+      const int ob = c / NN, ib = c % NN;
+      T v;
+      if (oa == ob) v = lc.Lself[oa ? tr : tl][ia][ib];
+      else if (oa == 0) v = (ia == k ? lc.ahi[ib] : T(0)) + (ib == 0 ? lc.ghi[ia] : T(0));  // test low cell, trial high
+      else v = (ia == 0 ? lc.alo[ib] : T(0)) + (ib == k ? lc.glo[ia] : T(0));             // test high cell, trial low
+      op.Lm[a * P + c] = v;
+    }
+    op.hlo[a] = op.hhi[a] = T(0);
+    op.lam[a] = lc.lamf[t][a];
+    op.mw[a] = lc.Mw[ia];
+    op.mu[a] = lc.Mu[ia];
+  }
+  for (int j = 0; j < NN; ++j) op.ma[j] = lc.Ma[j];
+  for (int j = 0; j < P; ++j)
+    for (int i = 0; i < P; ++i) op.S[j * P + i] = lc.Sf[t][j][i];
+  op.first = 0;
+  op.last = P - 1;
+  if constexpr (sizeof(T) == 4) {
+    for (int q = 0; q < P / 2; ++q) {
+      for (int j = 0; j < P; ++j) {
+        op.S2[j * (P / 2) + q] = make_float2(op.S[j * P + 2 * q], op.S[j * P + 2 * q + 1]);
+        op.St2[q * P + j] = make_float2(op.S[2 * q * P + j], op.S[(2 * q + 1) * P + j]);
+      }
+      for (int c = 0; c < P; ++c) op.L2[q * P + c] = make_float2(op.Lm[2 * q * P + c], op.Lm[(2 * q + 1) * P + c]);
+      op.mw2[q] = make_float2(op.mw[2 * q], op.mw[2 * q + 1]);
+      op.mu2[q] = make_float2(op.mu[2 * q], op.mu[2 * q + 1]);
+    }
+  }
+}
+
+// Interior patches (no end on the domain boundary): the clamped basis B
+// vanishes on the two patch-end nodes of each direction, so B^T r_D needs
+// the residual only on the other p = 2k rows and the correction lives there:
+// the pass is the interior (Dirichlet-row) layout of the kernel with the rows
+// 1..2n-2 of A_D (no halo: consistent = 0), of B S_m (zero columns beyond m)
+// and Lambda.
+template <int NN, typename T>
+void make_ops_clamped_interior(const LevelConst<T>& lc, Ops1D<2 * NN - 2, 2 * NN, T>& op) {
+  constexpr int P = 2 * NN, PO = 2 * NN - 2;
+  Ops1D<P, P, T> full;
+  make_ops_clamped<NN, T>(lc, 0, full);
+  for (int r = 0; r < PO; ++r) {
+    for (int c = 0; c < P; ++c) op.Lm[r * P + c] = full.Lm[(r + 1) * P + c];
+    op.hlo[r] = op.hhi[r] = T(0);
+    op.lam[r] = full.lam[r];
+    op.mw[r] = full.mw[r + 1];
+    op.mu[r] = full.mu[r + 1];
+  }
+  for (int j = 0; j < NN; ++j) op.ma[j] = lc.Ma[j];
+  for (int j = 0; j < PO; ++j)
+    for (int i = 0; i < PO; ++i) op.S[j * PO + i] = full.S[(j + 1) * P + i];
+  op.first = 0;
+  op.last = PO - 1;
+  if constexpr (sizeof(T) == 4) {
+    for (int q = 0; q < PO / 2; ++q) {
+      for (int j = 0; j < PO; ++j) {
+        op.S2[j * (PO / 2) + q] = make_float2(op.S[j * PO + 2 * q], op.S[j * PO + 2 * q + 1]);
+        op.St2[q * PO + j] = make_float2(op.S[2 * q * PO + j], op.S[(2 * q + 1) * PO + j]);
+      }
+      for (int c = 0; c < P; ++c) op.L2[q * P + c] = make_float2(op.Lm[2 * q * P + c], op.Lm[(2 * q + 1) * P + c]);
+      op.mw2[q] = make_float2(op.mw[2 * q], op.mw[2 * q + 1]);
+      op.mu2[q] = make_float2(op.mu[2 * q], op.mu[2 * q + 1]);
+    }
+  }
+}
+
+// One clamped colour pass (3D FP32): interior patches in the interior layout
+// on the calling stream, patches touching the domain boundary in the
+// boundary layout (all 2n rows) beside them on the second stream (the two
+// sets tile disjoint cells and read only their own cells).
+template <int NN, typename T>
+cudaError_t launch_int3_clamped(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s) {
+  using CI = I3<NN, T, false, 0>;
+  using CB = I3<NN, T, true, 0>;
+  const PatchGrid g = make_grid(3, h->lv[level].N, colour);
+  if (g.n_int + g.n_bnd <= 0) return cudaSuccess;
+  const int N = h->lv[level].N;
+  const long long nd = (long long)h->lv[level].ndofs;
+  cudaError_t e;
+  const bool fork = g.n_int > 0 && g.n_bnd > 0 && h->side;
+  cudaStream_t sb = fork ? h->side : s;
+  if (fork) {
+    if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+  }
+  if (g.n_int > 0) {
+    e = smem_opt_in(reinterpret_cast<const void*>(smooth_int3_kernel<NN, T, false, 0>), (int)CI::SMEM);
+    if (e != cudaSuccess) return e;
+    SmoothOps<CI::PO, CI::P, T, 1> ops;
+    make_ops_clamped_interior<NN, T>(h->hcst<T>(level), ops.t[0]);
+    dim3 grid((unsigned)((g.n_int + CI::PPC - 1) / CI::PPC), h->prm.nrhs);
+    smooth_int3_kernel<NN, T, false, 0><<<grid, CI::THREADS, CI::SMEM, s>>>(ops, colour, b, x, N, 0, nd, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (g.n_bnd > 0) {
+    e = smem_opt_in(reinterpret_cast<const void*>(smooth_int3_kernel<NN, T, true, 0>), (int)CB::SMEM);
+    if (e != cudaSuccess) return e;
+    SmoothOps<CB::PO, CB::P, T, CB::NT> ops;
+    for (int t = 0; t < CB::NT; ++t) make_ops_clamped<NN, T>(h->hcst<T>(level), t, ops.t[t]);
+    dim3 grid((unsigned)((g.n_bnd + CB::PPC - 1) / CB::PPC), h->prm.nrhs);
+    smooth_int3_kernel<NN, T, true, 0><<<grid, CB::THREADS, CB::SMEM, sb>>>(ops, colour, b, x, N, 0, nd, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (fork) {
+    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}

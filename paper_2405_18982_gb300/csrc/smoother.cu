@@ -6,6 +6,9 @@ template <int DIM, typename T, int NN>
 cudaError_t smooth_colour_n(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s);
 template <int DIM, typename T, int NN>
 cudaError_t smooth_step_n(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s);
+template <int NN>
+cudaError_t clamped_colour3_n(const sipg_handle* h, int level, int colour, const float* b, float* x,
+                              cudaStream_t s);
 
 namespace {
 
@@ -37,11 +40,33 @@ cudaError_t step_dim(const sipg_handle* h, int level, int reverse, const T* b, T
   return cudaErrorInvalidValue;
 }
 
+// The clamped kernel's fused colour pass (3D FP32); cudaErrorNotSupported
+// elsewhere (the caller then runs the residual-per-colour path).
+template <typename T>
+cudaError_t clamped_fused(const sipg_handle* h, int level, int colour, const T* b, T* x, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (h->prm.dim != 3) return cudaErrorNotSupported;
+    switch (h->n) {
+      case 3: return clamped_colour3_n<3>(h, level, colour, b, x, s);
+      case 4: return clamped_colour3_n<4>(h, level, colour, b, x, s);
+      case 5: return clamped_colour3_n<5>(h, level, colour, b, x, s);
+      case 6: return clamped_colour3_n<6>(h, level, colour, b, x, s);
+      case 7: return clamped_colour3_n<7>(h, level, colour, b, x, s);
+      case 8: return clamped_colour3_n<8>(h, level, colour, b, x, s);
+    }
+  }
+  return cudaErrorNotSupported;
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_smooth_colour(const sipg_handle* h, int level, int colour, const T* b, T* x,
                                  cudaStream_t s) {
+  if (h->prm.smoother == SIPG_SMOOTHER_CLAMPED) {
+    const cudaError_t e = clamped_fused<T>(h, level, colour, b, x, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (h->prm.smoother == SIPG_SMOOTHER_FULL || h->prm.smoother == SIPG_SMOOTHER_CLAMPED) {
     int nl = 0;
     return launch_full_colour<T>(h, level, colour, b, x, s, &nl);
@@ -60,8 +85,11 @@ cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, con
   if (h->prm.smoother == SIPG_SMOOTHER_FULL || h->prm.smoother == SIPG_SMOOTHER_CLAMPED) {
     *launches = 0;
     for (int i = 0; i < nc; ++i) {
-      int nl = 0;
-      cudaError_t e = launch_full_colour<T>(h, level, reverse ? nc - 1 - i : i, b, x, s, &nl);
+      const int c = reverse ? nc - 1 - i : i;
+      int nl = 1;
+      cudaError_t e = cudaErrorNotSupported;
+      if (h->prm.smoother == SIPG_SMOOTHER_CLAMPED) e = clamped_fused<T>(h, level, c, b, x, s);
+      if (e == cudaErrorNotSupported) e = launch_full_colour<T>(h, level, c, b, x, s, &nl);
       *launches += nl;
       if (e != cudaSuccess) return e;
     }

@@ -1111,6 +1111,17 @@ template <int DIM, typename T, int NN>
 cudaError_t smooth_step_n(const sipg_handle* h, int level, int reverse, const T* b, T* x, cudaStream_t s) {
   return step_dispatch2<T, DIM, NN>(h, level, reverse, b, x, s);
 }
+// One fused clamped-kernel colour pass (3D FP32): cudaErrorNotSupported where
+// the register-direct kernel does not apply (alignment, patch count).
+template <int NN>
+cudaError_t clamped_colour3_n(const sipg_handle* h, int level, int colour, const float* b, float* x,
+                              cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(b) % 16) != 0 || (reinterpret_cast<uintptr_t>(x) % 16) != 0)
+    return cudaErrorNotSupported;
+  return launch_int3_clamped<NN, float>(h, level, colour, b, x, s);
+}
+#define SIPG_CLAMPED_INST(NN)                                                                                 \
+  template cudaError_t clamped_colour3_n<NN>(const sipg_handle*, int, int, const float*, float*, cudaStream_t);
 
 #define SIPG_SMOOTH_INST(DIM, T, NN)                                                                         \
   template cudaError_t smooth_colour_n<DIM, T, NN>(const sipg_handle*, int, int, const T*, T*, cudaStream_t); \
