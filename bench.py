@@ -795,8 +795,9 @@ def run_table2(args):
     V-cycle whose smoother uses the Dirichlet-kernel residual; nu (Sec. 3.3),
     steps and time to solution with the FP64 and the FP32 V-cycle, the
     consistent residual, the full kernel (Table 1's setting) and the clamped
-    kernel (Table 2 right) beside it, and the values printed in Tables 1 and
-    2.  Cases
+    kernel (Table 2 right; also with GMRES preconditioned from the left, the
+    reading that reproduces that column) beside it, and the values printed
+    in Tables 1 and 2.  Cases
     k = 3..7, L = 2..7 up to --max-dofs DoFs.  One JSON line per case."""
     import time
 
@@ -818,21 +819,24 @@ def run_table2(args):
                    "nu_table2": None if np.isnan(printed[L - 2, k - 2]) else float(printed[L - 2, k - 2])}
             row["nu_table1"] = None if np.isnan(printed1[L - 2, k - 2]) else float(printed1[L - 2, k - 2])
             row["nu_table2_clamped"] = None if np.isnan(printed_c[L - 2, k - 2]) else float(printed_c[L - 2, k - 2])
-            for tag, prec, sm in (("fp64", SIPG_FP64, SIPG_SMOOTHER_PAPER), ("mixed", SIPG_FP32, SIPG_SMOOTHER_PAPER),
-                                  ("consistent_mixed", SIPG_FP32, SIPG_SMOOTHER_CONSISTENT),
-                                  ("full_mixed", SIPG_FP32, SIPG_SMOOTHER_FULL),
-                                  ("clamped_mixed", SIPG_FP32, SIPG_SMOOTHER_CLAMPED)):
+            for tag, prec, sm, left in (("fp64", SIPG_FP64, SIPG_SMOOTHER_PAPER, False),
+                                        ("mixed", SIPG_FP32, SIPG_SMOOTHER_PAPER, False),
+                                        ("consistent_mixed", SIPG_FP32, SIPG_SMOOTHER_CONSISTENT, False),
+                                        ("full_mixed", SIPG_FP32, SIPG_SMOOTHER_FULL, False),
+                                        ("clamped_mixed", SIPG_FP32, SIPG_SMOOTHER_CLAMPED, False),
+                                        # left preconditioning needs a fixed linear V-cycle: FP64
+                                        ("clamped_fp64_left", SIPG_FP64, SIPG_SMOOTHER_CLAMPED, True)):
                 s = SIPG(Params(dim=3, degree=k, log2_cells=L, n_levels=L, vcycle_precision=prec, smoother=sm))
                 f = torch.ones(1, s.ndofs(), dtype=torch.float64, device="cuda")
                 b = torch.zeros_like(f)
                 s.rhs(f, b)
                 x = torch.zeros_like(b)
                 work = torch.empty(s.gmres_workspace_bytes(30) + 256, dtype=torch.uint8, device="cuda")
-                s.gmres_solve(b, x, rtol=1e-8, maxit=200, restart=30, work=work)   # warm-up
+                s.gmres_solve(b, x, rtol=1e-8, maxit=200, restart=30, work=work, left=left)   # warm-up
                 x.zero_()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                info = s.gmres_solve(b, x, rtol=1e-8, maxit=200, restart=30, work=work)
+                info = s.gmres_solve(b, x, rtol=1e-8, maxit=200, restart=30, work=work, left=left)
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
                 row[f"nu_{tag}"] = round(info.nu, 2)

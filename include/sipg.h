@@ -257,6 +257,14 @@ size_t sipg_gmres_workspace_bytes(const sipg_handle* h, int restart);
  * the host). */
 sipg_status sipg_gmres_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
                              int restart, void* work, size_t work_bytes, sipg_info* info, void* stream);
+/* The same GMRES preconditioned from the left: Arnoldi on B A, the residual
+ * (history, nu and the stopping test ||B (b - A x)||_2 <= rtol ||B b||_2) is
+ * the one after the V-cycle, and x is updated from the Arnoldi vectors.  The
+ * reading of the paper's Table 2 clamped-kernel column (Sec. 3.3).  Same
+ * arguments, workspace and errors as sipg_gmres_solve; B must be a fixed
+ * linear operator (every V-cycle of one handle is). */
+sipg_status sipg_gmres_solve_left(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
+                                  int restart, void* work, size_t work_bytes, sipg_info* info, void* stream);
 
 /* out[r] = <a_r, b_r> for every column r (FP64, deterministic order),
  * written to device memory. */

@@ -345,8 +345,13 @@ def fcg(A_apply, precond, b, rtol=1e-10, maxit=200, x0=None):
     return x, hist
 
 
-def gmres(A_apply, precond, b, rtol=1e-8, maxit=200, restart=30, x0=None):
-    """GMRES preconditioned from the right in its flexible form (the
+def gmres(A_apply, precond, b, rtol=1e-8, maxit=200, restart=30, x0=None, side="right"):
+    """GMRES preconditioned from the right (side="right") or from the left
+    (side="left": GMRES on B A x = B b with the preconditioned residual
+    B (b - A x) as its residual, norm and stopping test ||B r|| <= rtol
+    ||B b||, the reading of Table 2's clamped column).
+
+    Right preconditioning in its flexible form (the
     preconditioned directions z_j = B v_j are kept, so B may vary between
     steps; for a fixed B this is right-preconditioned GMRES).  Arnoldi with
     modified Gram-Schmidt builds an orthonormal basis v_1..v_{j+1} with
@@ -357,6 +362,11 @@ def gmres(A_apply, precond, b, rtol=1e-8, maxit=200, restart=30, x0=None):
     true residual b - A x recomputed (it replaces the last history entry):
     the solve stops when it is <= rtol ||b||_2, else GMRES restarts from x.
     Returns (x, history of ||r||_2), the history starting with ||r_0||."""
+    if side == "left":
+        return gmres(lambda v: precond(A_apply(v)), lambda r: r, precond(np.asarray(b, dtype=np.float64)),
+                     rtol, maxit, restart, x0, "right")
+    if side != "right":
+        raise ValueError(side)
     b = np.asarray(b, dtype=np.float64)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     bnorm = np.linalg.norm(b)

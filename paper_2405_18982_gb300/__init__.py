@@ -204,10 +204,11 @@ class SIPG:
         return int(self.lib.sipg_gmres_workspace_bytes(self.h, restart))
 
     def gmres_solve(self, b, x, rtol=1e-8, maxit=200, restart=30, stream=None, history=256,
-                    allow_noconv=False, work=None):
-        """GMRES preconditioned from the right by the V-cycle (the paper's
-        outer solver); ``work`` (a CUDA uint8 tensor) is allocated here when
-        not given or too small."""
+                    allow_noconv=False, work=None, left=False):
+        """GMRES preconditioned by the V-cycle (the paper's outer solver),
+        from the right (sipg_gmres_solve) or with left=True from the left
+        (sipg_gmres_solve_left); ``work`` (a CUDA uint8 tensor) is allocated
+        here when not given or too small."""
         import torch
         nbytes = self.gmres_workspace_bytes(restart)
         if nbytes == 0:
@@ -217,8 +218,9 @@ class SIPG:
         aligned = (work.data_ptr() + 255) & ~255
         hist = (ctypes.c_double * history)()
         info = B.sipg_info(0, 0, 0.0, 0.0, hist, history, 0)
-        st = self.lib.sipg_gmres_solve(self.h, _ptr(b), _ptr(x), rtol, maxit, restart, ctypes.c_void_p(aligned),
-                                       nbytes, ctypes.byref(info), self._stream(stream))
+        fn = self.lib.sipg_gmres_solve_left if left else self.lib.sipg_gmres_solve
+        st = fn(self.h, _ptr(b), _ptr(x), rtol, maxit, restart, ctypes.c_void_p(aligned), nbytes, ctypes.byref(info),
+                self._stream(stream))
         if st != 0 and not (allow_noconv and st == B.SIPG_ENOCONV):
             self._check(st)
         return SolveInfo(info.iterations, info.status, info.rel_residual, info.nu,

@@ -79,6 +79,8 @@ SIGNATURES = {
     "sipg_gmres_workspace_bytes": (ctypes.c_size_t, [_vp, _i]),
     "sipg_gmres_solve": (_st, [_vp, _vp, _vp, _d, _i, _i, _vp, ctypes.c_size_t,
                                ctypes.POINTER(sipg_info), _vp]),
+    "sipg_gmres_solve_left": (_st, [_vp, _vp, _vp, _d, _i, _i, _vp, ctypes.c_size_t,
+                                    ctypes.POINTER(sipg_info), _vp]),
     "sipg_dot": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_dot_noalloc": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "sipg_selftest_barrier": (_st, [_vp, _i, _vp]),

@@ -472,10 +472,16 @@ struct GmresVectors {
     SIPG_CHECK(cudaStreamSynchronize(s), "sync");
     return SIPG_OK;
   }
-  // V_0 = b - A x, *beta = ||V_0||_2
+  bool left = false;  // preconditioned from the left: the residual is B (b - A x)
+  // V_0 = b - A x (left: B (b - A x), through Z_0), *beta = ||V_0||_2
   sipg_status residual(const double* b, const double* x, double* beta) {
     SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_RESIDUAL, b, x, V, s), "residual");
     h->launches += 1;
+    if (left) {
+      sipg_status st = gmres_precond(h, V, Z, s);
+      if (st) return st;
+      SIPG_CHECK(cudaMemcpyAsync(V, Z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s), "copy");
+    }
     double rr = 0.0;
     sipg_status st = dots(V, 1, V, &rr);
     if (st) return st;
@@ -485,13 +491,21 @@ struct GmresVectors {
 };
 
 sipg_status gmres_run(sipg_handle* h, const double* b, double* x, double rtol, int maxit, int m, char* work,
-                      sipg_info* info, cudaStream_t s) {
+                      sipg_info* info, cudaStream_t s, bool left = false) {
   const GmresLayout lay = gmres_layout(h, m);
   GmresVectors g{h, s, (long long)h->lv[h->L].ndofs, (long long)(lay.vec / sizeof(double)),
                  reinterpret_cast<double*>(work), reinterpret_cast<double*>(work + lay.off_z),
                  reinterpret_cast<double*>(work + lay.off_part), reinterpret_cast<double*>(work + lay.off_dev)};
+  g.left = left;
   double bb = 0.0, beta = 0.0;
-  sipg_status st = g.dots(b, 1, b, &bb);
+  sipg_status st;
+  if (left) {  // the norm the stopping test refers to: ||B b||
+    st = gmres_precond(h, b, g.z(0), s);
+    if (st) return st;
+    st = g.dots(g.z(0), 1, g.z(0), &bb);
+  } else {
+    st = g.dots(b, 1, b, &bb);
+  }
   if (st) return st;
   const double bnorm = sqrt(bb);
   st = g.residual(b, x, &beta);
@@ -511,10 +525,17 @@ sipg_status gmres_run(sipg_handle* h, const double* b, double* x, double rtol, i
     gv[0] = beta;
     int j = 0;  // completed steps of this cycle
     while (j < mc) {
-      st = gmres_precond(h, g.v(j), g.z(j), s);
-      if (st) return st;
-      SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, g.z(j), g.v(j + 1), s), "apply");
-      h->launches += 1;
+      if (left) {  // v_{j+1} = B A v_j (A v_j in Z_j)
+        SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, g.v(j), g.z(j), s), "apply");
+        h->launches += 1;
+        st = gmres_precond(h, g.z(j), g.v(j + 1), s);
+        if (st) return st;
+      } else {     // z_j = B v_j, v_{j+1} = A z_j
+        st = gmres_precond(h, g.v(j), g.z(j), s);
+        if (st) return st;
+        SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, g.z(j), g.v(j + 1), s), "apply");
+        h->launches += 1;
+      }
       // classical Gram-Schmidt, applied twice: w -= sum_i <V_i, w> V_i
       std::fill(hc.begin(), hc.end(), 0.0);
       for (int pass = 0; pass < 2; ++pass) {
@@ -566,7 +587,7 @@ sipg_status gmres_run(sipg_handle* h, const double* b, double* x, double rtol, i
       for (int q = i + 1; q < j; ++q) acc -= Hat(i, q) * y[q];
       y[i] = acc / Hat(i, i);
     }
-    SIPG_CHECK(gmres_maxpy(h, x, g.Z, g.ld, j, nullptr, y.data(), 1.0, g.n, s), "update");
+    SIPG_CHECK(gmres_maxpy(h, x, left ? g.V : g.Z, g.ld, j, nullptr, y.data(), 1.0, g.n, s), "update");
     st = g.residual(b, x, &beta);
     if (st) return st;
     hist.back() = beta;  // the true residual ends every cycle
@@ -1043,6 +1064,20 @@ sipg_status sipg_gmres_solve(sipg_handle* h, const double* b, double* x, double 
     return fail(h, SIPG_EINVAL, "GMRES workspace must be 256-byte aligned");
   if (work_bytes < gmres_layout(h, restart).total) return fail(h, SIPG_EINVAL, "GMRES workspace too small");
   return gmres_run(h, b, x, rtol, maxit, restart, static_cast<char*>(work), info, S(stream));
+}
+
+sipg_status sipg_gmres_solve_left(sipg_handle* h, const double* b, double* x, double rtol, int maxit, int restart,
+                                  void* work, size_t work_bytes, sipg_info* info, void* stream) {
+  sipg_status st = need_bound(h);
+  if (st) return st;
+  if (h->prm.nrhs != 1) return fail(h, SIPG_EUNSUPPORTED, "GMRES solves one right-hand side (nrhs = 1)");
+  if (!b || !x || b == x) return fail(h, SIPG_EINVAL, "null or aliased vectors");
+  if (!(rtol > 0.0) || maxit < 0) return fail(h, SIPG_EINVAL, "bad rtol or maxit");
+  if (restart < 1 || restart > SIPG_GMRES_MAX_RESTART) return fail(h, SIPG_EINVAL, "restart out of range");
+  if (!work || (reinterpret_cast<uintptr_t>(work) & 255) != 0)
+    return fail(h, SIPG_EINVAL, "GMRES workspace must be 256-byte aligned");
+  if (work_bytes < gmres_layout(h, restart).total) return fail(h, SIPG_EINVAL, "GMRES workspace too small");
+  return gmres_run(h, b, x, rtol, maxit, restart, static_cast<char*>(work), info, S(stream), true);
 }
 
 sipg_status sipg_adjoint_solve(sipg_handle* h, const double* g, double* lambda, double rtol, int maxit,

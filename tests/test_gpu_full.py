@@ -119,26 +119,32 @@ def test_table1_setting_on_device():
 
 
 def test_table2_clamped_setting_on_device():
-    # Table 2, clamped kernel: at L = 3 the device reproduces the oracle's nu
-    # (the same subspace correction, nu measured in the Lagrange basis); at
-    # L = 5 nu stays level-independent (within 20 % of the oracle's L = 3
-    # value; the oracle gives 41.1 and 40.8 at L = 3 and 4), above the
-    # Dirichlet kernel's, and within 2.5x of the table (the change of basis
-    # of the residual norm: 41.1 against 22.7 at L = 3)
+    # Table 2, clamped kernel, with GMRES preconditioned from the left (the
+    # reading under which the oracle reproduces the clamped column): at L = 3
+    # the device reproduces the oracle's left-preconditioned history and nu;
+    # at L = 5 (Q3 on 32^3 cells) nu is within 20 % of the printed 19.0,
+    # not above the L = 3 value (the printed column falls from 22.7 to 19.0)
+    # and above the Dirichlet kernel's.  The right-preconditioned device GMRES still
+    # reproduces the oracle's right-preconditioned nu at L = 3.
     import torch
     ref = np.loadtxt(os.path.join(GOLDEN, "table2_clamped_nu.txt"))
     k, L = 3, 3
     N = 1 << L
     H = Hierarchy(3, k, N, L, variant="clamped")
     b = rhs_from_nodal(3, k, N, np.ones(H.A.shape[0]))
-    _, h_ref = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=100, restart=64)
-    nu3 = fractional_iterations(h_ref)
     s = make(3, k, L, L, smoother=SIPG_SMOOTHER_CLAMPED)
-    info = s.gmres_solve(dev(b), dev(np.zeros_like(b)), rtol=1e-8, maxit=100, restart=64)
-    assert info.status == 0
-    # 42 GMRES steps: the last residual carries the rounding difference of
-    # the local solves amplified by the residual reduction
-    assert abs(info.nu - nu3) <= 1e-3 * nu3
+    nu3 = {}
+    for left in (True, False):
+        _, h_ref = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=100, restart=64,
+                         side="left" if left else "right")
+        nu3[left] = fractional_iterations(h_ref)
+        info = s.gmres_solve(dev(b), dev(np.zeros_like(b)), rtol=1e-8, maxit=100, restart=64, left=left)
+        assert info.status == 0 and info.iterations == len(h_ref) - 1
+        # up to 42 GMRES steps: the last residual carries the rounding
+        # difference of the local solves amplified by the residual reduction
+        assert abs(info.nu - nu3[left]) <= 1e-3 * nu3[left], (left, info.nu, nu3[left])
+        h = np.array(info.history[:len(h_ref)])
+        assert np.allclose(h, h_ref, rtol=1e-5, atol=1e-12 * h_ref[0])
     L = 5
     nus = {}
     for sm in (SIPG_SMOOTHER_CLAMPED, 1):
@@ -146,10 +152,10 @@ def test_table2_clamped_setting_on_device():
         f = torch.ones(1, s.ndofs(), dtype=torch.float64, device="cuda")
         bd = torch.zeros_like(f)
         s.rhs(f, bd)
-        info = s.gmres_solve(bd, torch.zeros_like(f), rtol=1e-8, maxit=200, restart=64)
+        info = s.gmres_solve(bd, torch.zeros_like(f), rtol=1e-8, maxit=200, restart=64, left=True)
         assert info.status == 0
         nus[sm] = info.nu
     printed = ref[L - 2, k - 2]
-    assert 0.8 * nu3 <= nus[SIPG_SMOOTHER_CLAMPED] <= 1.2 * nu3, (nus, nu3)
-    assert printed / 2.5 <= nus[SIPG_SMOOTHER_CLAMPED] <= printed * 2.5, (nus, printed)
+    assert abs(nus[SIPG_SMOOTHER_CLAMPED] - printed) <= 0.2 * printed, (nus, printed)
+    assert nus[SIPG_SMOOTHER_CLAMPED] <= nu3[True], (nus, nu3)
     assert nus[SIPG_SMOOTHER_CLAMPED] > nus[1]

@@ -329,6 +329,32 @@ def test_gmres_history_is_the_krylov_minimum():
         assert np.allclose(x, np.linalg.solve(A, b), rtol=0, atol=1e-10 * np.abs(np.linalg.solve(A, b)).max())
 
 
+def test_left_gmres_history_is_the_preconditioned_krylov_minimum():
+    # GMRES preconditioned from the left minimises ||B (b - A x)|| over x in
+    # the Krylov space K_j(B A, B b): its history equals that brute-force
+    # minimum (a different norm from the right-preconditioned one)
+    from oracle.mg import gmres
+    rng = np.random.default_rng(23)
+    n = 30
+    A = 4.0 * np.eye(n) + 0.6 * rng.standard_normal((n, n))
+    Bm = np.linalg.inv(A + 0.8 * rng.standard_normal((n, n)) / np.sqrt(n))
+    b = rng.standard_normal(n)
+    x, hist = gmres(lambda v: A @ v, lambda v: Bm @ v, b, rtol=1e-12, maxit=n, restart=n, side="left")
+    assert hist[0] == pytest.approx(np.linalg.norm(Bm @ b))
+    # (B A is close to the identity here, so the residual falls fast; the
+    # brute-force Krylov basis is compared while it is well conditioned)
+    checked = 0
+    for j in range(1, len(hist)):
+        if hist[j] < 1e-4 * hist[0]:
+            break
+        assert abs(hist[j] - _krylov_min_residual(Bm @ A, Bm @ b, j)) <= 1e-9 * np.linalg.norm(Bm @ b)
+        checked += 1
+    assert checked >= 4
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=0, atol=1e-9 * np.abs(np.linalg.solve(A, b)).max())
+    _, right = gmres(lambda v: A @ v, lambda v: Bm @ v, b, rtol=1e-12, maxit=n, restart=n)
+    assert abs(hist[3] - right[3]) > 1e-6 * hist[0]      # not the right-preconditioned history
+
+
 def test_gmres_restarts_and_converges():
     from oracle.mg import gmres
     rng = np.random.default_rng(22)
@@ -548,26 +574,31 @@ def test_clamped_local_solve_and_order(dim, k, N):
     assert np.allclose(ref, other, rtol=0, atol=1e-12 * np.abs(ref).max())
 
 
-def test_gmres_clamped_kernel_near_table2():
-    # Table 2, clamped kernel: many more iterations than the Dirichlet kernel
-    # at low degree, fewer as k grows.  The oracle measures the residual in
-    # the Lagrange basis (the paper: a Hermite-type basis), so the printed
-    # values are matched to a factor 2 only (Q3: 31.5 against 18.6)
+def test_gmres_clamped_kernel_reproduces_table2():
+    # Table 2, clamped kernel, read with GMRES preconditioned from the left
+    # (its residual, and so nu, measured after the V-cycle): within 20 % of
+    # the printed values for Q3 at L = 3 and Q5 at L = 2, within 40 % for Q3
+    # at L = 2 (the 4^3 mesh, where 26 of the 27 patches touch the domain
+    # boundary), nu level-independent as printed.  Preconditioned from the
+    # right (the Euclidean residual) the same V-cycle gives nu 1.7-1.9 times
+    # the printed values and growing with L; writing the system in a
+    # Hermite-type basis (value and derivative at the cell ends) moves nu by
+    # only ~15 % -- neither explains the column.
     from oracle.assembly import rhs_from_nodal
     from oracle.mg import gmres
     ref = np.loadtxt(os.path.join(GOLDEN, "table2_clamped_nu.txt"))
     dirichlet = np.loadtxt(os.path.join(GOLDEN, "table2_dirichlet_nu.txt"))
     nus = {}
-    for k in (3, 4):
-        N, L = 4, 2
+    for k, N, L, tol in ((3, 8, 3, 0.2), (5, 4, 2, 0.2), (3, 4, 2, 0.4)):
         H = Hierarchy(3, k, N, L, variant="clamped")
         b = rhs_from_nodal(3, k, N, np.ones(H.A.shape[0]))
-        _, hist = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=100)
-        nus[k] = fractional_iterations(hist)
+        _, hist = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-8, maxit=100, side="left")
+        nus[(k, L)] = fractional_iterations(hist)
         printed = ref[L - 2, k - 2]
-        assert printed / 2 <= nus[k] <= printed * 2, (k, nus[k], printed)
-        assert nus[k] > dirichlet[L - 2, k - 2]      # the paper's ordering at low degree
-    assert nus[4] < nus[3]
+        assert abs(nus[(k, L)] - printed) <= tol * printed, (k, L, nus[(k, L)], printed)
+        assert nus[(k, L)] > dirichlet[L - 2, k - 2]      # the paper's ordering
+    assert nus[(5, 2)] < nus[(3, 2)]                      # falls with the degree
+    assert abs(nus[(3, 3)] - nus[(3, 2)]) < 0.2 * nus[(3, 2)]   # no growth with L
 
 
 def test_clamped_space_closed_form_for_q2():
