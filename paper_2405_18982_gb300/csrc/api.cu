@@ -659,7 +659,11 @@ sipg_status tune_T(sipg_handle* h, cudaStream_t s) {
       int path, tile;
     };
     std::vector<Cand> cands = {{1, 0}};
-    if (h->prm.dim == 3 && sizeof(T) == 4) cands.push_back({1, 1});
+    if (h->prm.dim == 3 && sizeof(T) == 4) {
+      cands.push_back({1, 1});
+      cands.push_back({1, 2});
+      cands.push_back({1, 3});
+    }
     if (h->fuse_small_levels) cands.push_back({0, 0});
     float best = 1e30f;
     Cand pick = {-1, 0};
@@ -758,7 +762,10 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   // colour; SIPG_AUTOTUNE=0 skips the bind-time timing of the launch paths
   if (const char* env = getenv("SIPG_FUSED_SMOOTHING")) h->fuse_small_levels = atoi(env) != 0;
   if (const char* env = getenv("SIPG_AUTOTUNE")) h->autotune = atoi(env) != 0;
-  if (const char* env = getenv("SIPG_TILE")) h->force_tile = atoi(env) == 1 ? 1 : 0;
+  if (const char* env = getenv("SIPG_TILE")) {
+    const int t = atoi(env);
+    h->force_tile = (t >= 0 && t <= 3) ? t : 0;
+  }
   h->n = n;
   h->L = L;
   for (int l = 0; l <= L; ++l) {

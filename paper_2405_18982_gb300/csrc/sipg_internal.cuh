@@ -111,7 +111,8 @@ struct sipg_handle {
   // autotuned choices per precision (0 FP64, 1 FP32) and level, measured at
   // bind time unless SIPG_AUTOTUNE=0: smoothing-step path (-1 not tuned,
   // 0 fused launch, 1 colour by colour) and interior tile of the 3D FP32
-  // colour pass (0 default patches per CTA, 1 half as many)
+  // colour pass (0 default patches per CTA, 1 half as many, 2 / 3 the default
+  // with b and x loaded ahead, at four / three CTAs per SM)
   bool autotune = true;
   std::vector<int> tune_path[2], tune_tile[2];
   int tuned_path(int prec, int l) const {

@@ -50,7 +50,9 @@ struct I3 {
   static constexpr int PREFIX = (DINV * (int)sizeof(T) + 15) / 16 * 16;
   // patches per CTA: fill about 54 KB of shared memory (four CTAs per SM) with
   // at most 512 threads
-  // (TILE = 1: half as many, for the autotuner)
+  // (TILE = 1: half as many, for the autotuner; TILE = 2, 3: the default
+  // tile with b and x on V_j loaded ahead of the sweeps that use them, at
+  // four and three CTAs per SM)
   static constexpr int ppc() {
     int k = (54 * 1024 - PREFIX) / (PS * (int)sizeof(T));
     if (k > 512 / TPP) k = 512 / TPP;
@@ -66,10 +68,11 @@ struct I3 {
     int m = by_smem < by_thr ? by_smem : by_thr;
     // boundary patches: longer lines need more registers; they run beside
     // the interior kernel
-    const int cap = BND ? 2 : (TILE == 1 ? 8 : 4);
+    const int cap = BND ? 2 : (TILE == 1 ? 8 : (TILE == 3 ? 3 : 4));
     return m < 1 ? 1 : (m > cap ? cap : m);
   }
   static constexpr int MINB = minblocks();
+  static constexpr bool PF = !BND && TILE >= 2;  // loads of b and x on V_j issued early
   static constexpr int VW = run_vw<NN, T>();
 };
 
@@ -122,7 +125,7 @@ __device__ __forceinline__ void int3_dinv(const Ops1D<2 * NN - 2, 2 * NN, T>& o0
 // read-only (non-coherent) path, valid when no other CTA writes what this
 // launch reads (one colour per launch); the fused step, whose later colours
 // read what other CTAs wrote, uses coherent loads.
-template <int NN, typename T, bool BND, int PPC, bool NC>
+template <int NN, typename T, bool BND, int PPC, bool NC, bool PF = false>
 __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT>& ops,
                                           const T* dinv, T* buf, long long pbase, int colour,
                                           const T* __restrict__ b, T* x, int N, int consistent,
@@ -229,6 +232,18 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       }
     });
   }
+  // PF: b on this thread's z line of V_j, loaded now so that the loads
+  // overlap the y sweep (interior patches: every row is in V_j)
+  T bvp[PO], xop[PO];
+  if constexpr (PF) {
+    if (valid) {
+      const int q0 = lane % PO, q1 = lane / PO;
+      const T* gbp = b + ((v[0] - 1) + (long long)N * ((v[1] - 1) + (long long)N * (v[2] - 1))) * ND +
+                     ((q0 + OFF) / NN) * ND + ((q1 + OFF) / NN) * cs1 + ((q0 + OFF) % NN) + ((q1 + OFF) % NN) * NN;
+#pragma unroll
+      for (int r2 = 0; r2 < PO; ++r2) bvp[r2] = __ldg(gbp + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN);
+    }
+  }
   __syncthreads();
 
   // ------------------------------------------------------------------ y sweep
@@ -302,7 +317,10 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
 #pragma unroll
       for (int r2 = 0; r2 < PO; ++r2) {
         const bool in = inxy && r2 >= zlo && r2 <= zhi;
-        bv[r2] = in ? __ldg(gb + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN) : T(0);
+        if constexpr (PF)
+          bv[r2] = bvp[r2];
+        else
+          bv[r2] = in ? __ldg(gb + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN) : T(0);
       }
 #pragma unroll
       for (int a2 = 0; a2 < P; ++a2) {
@@ -319,6 +337,12 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       st_rows2<PO>(oz.S2, o, t1);
 #pragma unroll
       for (int k2 = 0; k2 < PO; ++k2) RA[ST * r1 + PO * k2 + r0] = t1[k2];
+      // PF: x on the same line, for the final update (only this patch
+      // writes it), loaded now so that the loads overlap the transforms
+      if constexpr (PF) {
+#pragma unroll
+        for (int r2 = 0; r2 < PO; ++r2) xop[r2] = ld_elem<NC>(gx + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN);
+      }
     });
   }
   __syncthreads();
@@ -384,7 +408,10 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
 #pragma unroll
       for (int r2 = 0; r2 < PO; ++r2) {
         const bool in = inxy && r2 >= zlo && r2 <= zhi;
-        xo[r2] = in ? gx[((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN] : T(0);
+        if constexpr (PF)
+          xo[r2] = xop[r2];
+        else
+          xo[r2] = in ? gx[((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN] : T(0);
       }
 #pragma unroll
       for (int k2 = 0; k2 < PO; ++k2) w[k2] = RB[ST * r1 + PO * k2 + r0];
@@ -408,7 +435,7 @@ __global__ void __launch_bounds__(I3<NN, T, BND, TILE>::THREADS, I3<NN, T, BND, 
   T* dinv = reinterpret_cast<T*>(smem_raw);
   if constexpr (!BND) int3_dinv<NN, T>(ops.t[0], dinv);  // read after the first CTA barrier of the body
   const long long col = (long long)blockIdx.y * ndofs;
-  int3_body<NN, T, BND, C::PPC, true>(ops, dinv, reinterpret_cast<T*>(smem_raw + C::PREFIX), (long long)blockIdx.x * C::PPC,
+  int3_body<NN, T, BND, C::PPC, true, C::PF>(ops, dinv, reinterpret_cast<T*>(smem_raw + C::PREFIX), (long long)blockIdx.x * C::PPC,
                                 colour, b + col, x + col, N, consistent, grid);
 }
 

@@ -930,7 +930,12 @@ cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T*
   if constexpr (DIM == 3 && sizeof(T) == 4) {
     if (use_int3<DIM, T>(g, b, x)) {
       if constexpr (!BND)
-        if (h->tuned_tile(1, level) == 1) return launch_int3<NN, T, BND, 1>(h, level, colour, b, x, g, s);
+        switch (h->tuned_tile(1, level)) {
+          case 1: return launch_int3<NN, T, BND, 1>(h, level, colour, b, x, g, s);
+          case 2: return launch_int3<NN, T, BND, 2>(h, level, colour, b, x, g, s);
+          case 3: return launch_int3<NN, T, BND, 3>(h, level, colour, b, x, g, s);
+          default: break;
+        }
       return launch_int3<NN, T, BND, 0>(h, level, colour, b, x, g, s);
     }
   }

@@ -10,7 +10,8 @@ domain-boundary patch, random interior ones) x - x0 equals the oracle's dense
 patch solve A_j^{-1} r_j to 1e-4 relative (FP32 fast diagonalisation of patch
 matrices with condition numbers up to ~1e3).  Each case runs with the
 launch path pinned (no autotuning, colour-by-colour launches) on both
-interior tiles of the 3D kernel, and with the autotuned choice.
+interior tiles of the 3D kernel (default, half, and the default with b and x
+loaded ahead at four and three CTAs per SM), and with the autotuned choice.
 
 Also: the two largest distinct members of the ragged 2D batch (2^9 x 2^9
 cells, k = 5, 6) through the batch's member handles, and the multi-RHS case
@@ -35,6 +36,8 @@ CASES = [(2, k, 7) for k in range(2, 8)] + [(3, k, 5) for k in range(2, 8)]
 IDS = [f"d{d}k{k}N{1 << l}" for d, k, l in CASES]
 PATHS = {"pinned": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "0"},
          "pinned_half_tile": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "1"},
+         "pinned_prefetch": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "2"},
+         "pinned_prefetch_3cta": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "3"},
          "tuned": {}}
 VARIANTS = {"consistent": SIPG_SMOOTHER_CONSISTENT, "paper": SIPG_SMOOTHER_PAPER}
 TOL = 1e-4
@@ -88,7 +91,7 @@ def check_colour_passes(s, level, dim, k, N, variant, seed, samples, colours=Non
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_smooth_colour_fp32(case, variant, path, monkeypatch):
     dim, k, l2 = case
-    if path == "pinned_half_tile" and dim == 2:
+    if path.startswith("pinned_") and path != "pinned" and dim == 2:
         pytest.skip("the 2D colour pass has one tile")
     for key, val in PATHS[path].items():
         monkeypatch.setenv(key, val)
