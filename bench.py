@@ -49,10 +49,12 @@ WORKLOAD = ("3D SIPG Poisson, unit cube, 64^3 cells, 6 levels, Q3 GLL (16.8M DoF
 # of the library built from sources whose digest is recorded here; reported
 # as null once any of those sources has changed since the capture
 TRAFFIC = {
-    "colour_pass": {"bytes": None, "sha": None,
+    # smooth_int3_kernel<4, float, interior, tile 3>: 126,973,952 read + 11,687,168 written
+    "colour_pass": {"bytes": 138661120, "sha": "e8846fb4708f77d2", "tiles": (0, 2, 3),
                     "sources": ["smooth_i_d3_f32_a.cu", "smoother_impl.cuh", "smooth_int3.cuh", "tensor_ops.cuh",
                                 "sipg_internal.cuh"]},
-    "fp64_apply": {"bytes": None, "sha": None,
+    # apply_kernel<3, 4, double>: 134,315,008 read + 98,545,920 written
+    "fp64_apply": {"bytes": 232860928, "sha": "d9b7aa0a3ba3dd9d",
                    "sources": ["apply.cu", "apply3.cuh", "tensor_ops.cuh", "sipg_internal.cuh"]},
 }
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
@@ -67,9 +69,15 @@ def source_digest(files):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(name):
+def measured_traffic(name, tile=None):
+    """The recorded DRAM bytes, or None when the kernel's sources changed
+    since the capture or (colour pass) the benched tile tiles the patches
+    differently from the captured one (tiles 0, 2, 3 share the patch tiling
+    and access pattern; the capture ran tile 3)."""
     t = TRAFFIC[name]
     if t["bytes"] is None or t["sha"] != source_digest(t["sources"]):
+        return None
+    if tile is not None and tile not in t.get("tiles", (tile,)):
         return None
     return t["bytes"]
 
@@ -369,11 +377,15 @@ def run_ours(args):
     l0 = s_mix.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
+    # (an NVTX range around the timed solves, so that a profiler's launch
+    # list can be restricted to them)
+    torch.cuda.nvtx.range_push("timed_mixed_solves")
     ev0.record(stream)
     for _ in range(args.steps):
         info = s_mix.solve(b, x, rtol=RTOL, maxit=200, zero_start=True)
         iters.append(info.iterations)
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
@@ -467,8 +479,10 @@ def run_ours(args):
 
     t_col = launch_time(lambda: s_mix.smooth_colour(L, 0, bf, xf))
     fl_survey, fl_sched, by_col, npatch0 = smoother_counts(DIM, K, N, 0, 4)
-    roof = roofline("smooth_int3_kernel<4,float,interior> (finest level, colour 0, %d patches)" % npatch0,
-                    fl_sched, by_col, t_col, peak32, "FP32", measured_traffic("colour_pass"),
+    _, tile = s_mix.tuning(L)
+    roof = roofline("smooth_int3_kernel<4,float,interior,tile %d> (finest level, colour 0, %d patches; the "
+                    "autotuner's tile)" % (tile, npatch0),
+                    fl_sched, by_col, t_col, peak32, "FP32", measured_traffic("colour_pass", tile),
                     {"survey_flops_per_launch": int(fl_survey),
                      "survey_alu_frac": round(fl_survey / t_col / 1e12 / peak32, 4),
                      "counts": "flops = kernel schedule (sum-factorised, rank-one mass, structural zeros "
@@ -514,6 +528,7 @@ def run_ours(args):
 
     # ---- C3: the degree-7 configuration with the FP32 and the TF32 V-cycle
     c3 = c3_record(torch, dev) if not args.no_c3 else None
+    c4a, c4b = c4_records(torch) if not args.no_c3 else (None, None)
 
     # ---- end to end through the public host-buffer call
     fh = f.detach().cpu().pin_memory()
@@ -554,6 +569,8 @@ def run_ours(args):
             "roofline_fp64_apply": roof_apply,
             "per_op": per_op,
             "c3_q7": c3,
+            "c4a_multirhs": c4a,
+            "c4b_ragged": c4b,
             "e2e": {"value": round(e2e_value, 2), "unit": "MDoF/s", "h2d_bytes_per_step": n * 8,
                     "d2h_bytes_per_step": n * 8,
                     "note": "sipg_solve_host: pinned f in, b = M f, solve from 0, u out"},
@@ -645,6 +662,79 @@ def run_kernel_only(args):
 
 
 # ----------------------------------------------------------------- batched runs
+def c4_records(torch, reps=2):
+    """C4a: 3D Q4 on 32^3 cells with 32 N(0,1) right-hand sides (seeds
+    100..131) in one mixed solve to 1e-10, next to one right-hand side alone.
+    C4b: the ragged batch of 64 independent 2D problems (2^L x 2^L cells, L
+    uniform in 5..9, degree uniform in 2..6, seed 4; f ~ N(0,1), seeds
+    1000 + i, b = M f), one batched mixed solve to 1e-10 (members on their own
+    streams with CUDA-graph iteration bodies), next to the members one after
+    another.  CUDA events around `reps` solves after one warm-up."""
+    from paper_2405_18982_gb300 import SIPG, SIPG_FP32, Params, SIPGBatch, inputs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    nrhs = 32
+    s = SIPG(Params(dim=3, degree=4, log2_cells=5, n_levels=5, vcycle_precision=SIPG_FP32, nrhs=nrhs, use_graphs=1))
+    one = SIPG(Params(dim=3, degree=4, log2_cells=5, n_levels=5, vcycle_precision=SIPG_FP32, use_graphs=1))
+    nd = s.ndofs()
+    b = torch.from_numpy(inputs.normal_columns(list(range(100, 100 + nrhs)), nd)).to("cuda")
+    x = torch.zeros_like(b)
+    b1 = b[:1].contiguous()
+    x1 = torch.zeros_like(b1)
+    ms_m, inf = timed(lambda: s.solve(b, x, rtol=1e-10, maxit=100, zero_start=True))
+    ms_1, inf1 = timed(lambda: one.solve(b1, x1, rtol=1e-10, maxit=100, zero_start=True))
+    c4a = {"workload": "3D Q4 32^3 (4.1M DoFs) x 32 RHS, mixed FCG to 1e-10", "ms_per_solve": round(ms_m, 3),
+           "MDoF_per_s": round(nd * nrhs / ms_m / 1e3, 1), "iterations": inf.iterations,
+           "rel_residual": inf.rel_residual, "single_rhs_ms_per_solve": round(ms_1, 3),
+           "single_MDoF_per_s": round(nd / ms_1 / 1e3, 1)}
+    s.close()
+    one.close()
+    del s, one, b, x
+    torch.cuda.empty_cache()
+
+    shapes = inputs.ragged_problems(4)
+    bt = SIPGBatch([Params(dim=2, degree=k, log2_cells=L, n_levels=L, vcycle_precision=SIPG_FP32, use_graphs=1)
+                    for L, k in shapes])
+    bs, xs = [], []
+    for i, m in enumerate(bt.members):
+        f = torch.from_numpy(inputs.normal(1000 + i, m.ndofs())).to("cuda").view(1, -1)
+        bb = torch.zeros_like(f)
+        m.rhs(f, bb)
+        bs.append(bb)
+        xs.append(torch.zeros_like(bb))
+    total = sum(m.ndofs() for m in bt.members)
+
+    def batched():
+        for xx in xs:
+            xx.zero_()
+        return bt.solve(bs, xs, rtol=1e-10, maxit=100)
+
+    def sequential():
+        return [m.solve(bb, xx, rtol=1e-10, maxit=100, zero_start=True) for m, bb, xx in zip(bt.members, bs, xs)]
+
+    ms_b, infos = timed(batched)
+    ms_s, _ = timed(sequential)
+    its = [i.iterations for i in infos]
+    c4b = {"workload": "64 ragged 2D problems, L in 5..9, k in 2..6 (seed 4), mixed FCG to 1e-10",
+           "total_dofs": total, "batched_ms_per_solve": round(ms_b, 3),
+           "sequential_ms_per_solve": round(ms_s, 3), "batched_MDoF_per_s": round(total / ms_b / 1e3, 1),
+           "iterations_min_max": [min(its), max(its)], "worst_rel_residual": max(i.rel_residual for i in infos)}
+    bt.close()
+    del bt, bs, xs
+    torch.cuda.empty_cache()
+    return c4a, c4b
+
+
 def run_batched(args):
     """--mode ragged: 64 independent 2D problems (2^L x 2^L cells, L uniform in
     5..9, degree uniform in 2..6, seeded), one mixed-precision batched solve to
@@ -970,7 +1060,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-c3", action="store_true", help="skip the degree-7 FP32 / TF32 record")
+    ap.add_argument("--no-c3", action="store_true", help="skip the C3 (degree 7) and C4 (batched) records")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "smooth", "apply", "vcycle", "levels", "ragged", "multirhs", "sweep", "table2",

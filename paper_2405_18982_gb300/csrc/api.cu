@@ -976,7 +976,9 @@ sipg_status sipg_smooth_colour(sipg_handle* h, int level, int prec, int colour, 
                       ? launch_smooth_colour<double>(h, level, colour, (const double*)b, (double*)x, S(stream))
                       : launch_smooth_colour<float>(h, level, colour, (const float*)b, (float*)x, S(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "smoother");
-  h->launches += 1;
+  const bool full = h->prm.smoother == SIPG_SMOOTHER_FULL ||
+                    (h->prm.smoother == SIPG_SMOOTHER_CLAMPED && !(h->prm.dim == 3 && prec == SIPG_FP32));
+  h->launches += full ? 2 : colour_kernels(h->prm.dim, h->lv[level].N, colour);
   return SIPG_OK;
 }
 

@@ -226,6 +226,9 @@ cudaError_t copy_or_zero(void* dst, size_t bytes, cudaStream_t s);
 // current device only, so the record is kept per device; a mutex guards it
 // against concurrent first calls from several host threads.
 cudaError_t smem_opt_in(const void* kernel, int bytes);
+// Kernels one Dirichlet- or clamped-kernel colour pass launches on a level of
+// N cells per direction (interior and domain-boundary patches).
+int colour_kernels(int dim, int N, int colour);
 // Interior patches of a 3D FP32 colour pass with the fast-diagonalisation
 // sweeps on the tensor cores (TF32); cudaErrorNotSupported where that kernel
 // does not apply (the caller then launches the FP32 kernel).

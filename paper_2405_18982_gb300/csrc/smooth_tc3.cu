@@ -423,14 +423,16 @@ cudaError_t launch_tc3_impl(const sipg_handle* h, int level, int colour, const f
                             const PatchGrid& g, cudaStream_t s) {
   using C = TC3<NN>;
   if (g.n_int <= 0) return cudaSuccess;
-  int per_sm = 0;
-  cudaError_t e = smem_opt_in_occupancy(reinterpret_cast<const void*>(smooth_tc3_kernel<NN>), C::NT, C::SMEM,
-                                        &per_sm);
+  cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(smooth_tc3_kernel<NN>), C::SMEM);
   if (e != cudaSuccess) return e;
-  if (per_sm <= 0 || h->num_sms <= 0) return cudaErrorNotSupported;
+  if (h->num_sms <= 0) return cudaErrorNotSupported;
   SmoothOps<C::PO, C::P, float, 1> ops;
   make_ops<C::PO, C::P, false, float>(h->hcst<float>(level), 0, ops.t[0]);
-  const long long cap = (long long)h->num_sms * per_sm;
+  // A non-cooperative persistent loop: up to six CTAs per SM (three are
+  // resident at a time by shared memory and registers; the others start as
+  // slots free up), each taking every gridDim.x-th patch.  (The occupancy
+  // query is not used here: it reported one CTA per SM for this kernel.)
+  const long long cap = (long long)h->num_sms * 6;
   const unsigned gx = (unsigned)(g.n_int < cap ? g.n_int : cap);
   int* status = reinterpret_cast<int*>(h->ws + h->off_sync + 2 * sizeof(unsigned int));
   smooth_tc3_kernel<NN><<<dim3(gx, h->prm.nrhs), C::NT, C::SMEM, s>>>(

@@ -60,6 +60,25 @@ cudaError_t clamped_fused(const sipg_handle* h, int level, int colour, const T* 
 
 }  // namespace
 
+// Kernels one colour pass launches: one for the interior patches and one for
+// the patches on the domain boundary, where the colour has any (the patch
+// enumeration of make_grid: per direction m in [0, cnt), interior box
+// [lo, hi)).
+int colour_kernels(int dim, int N, int colour) {
+  long long tot = 1, inner = 1;
+  for (int e = 0; e < dim; ++e) {
+    const int par = (colour >> e) & 1;
+    const int cnt = par ? N / 2 : N / 2 - 1;
+    const int lo = par ? 1 : 0;
+    int hi = N / 2 - 1;
+    if (hi < lo) hi = lo;
+    tot *= cnt > 0 ? cnt : 0;
+    inner *= hi - lo;
+  }
+  if (tot <= 0) return 0;
+  return (inner > 0 ? 1 : 0) + (tot - inner > 0 ? 1 : 0);
+}
+
 template <typename T>
 cudaError_t launch_smooth_colour(const sipg_handle* h, int level, int colour, const T* b, T* x,
                                  cudaStream_t s) {
@@ -86,7 +105,7 @@ cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, con
     *launches = 0;
     for (int i = 0; i < nc; ++i) {
       const int c = reverse ? nc - 1 - i : i;
-      int nl = 1;
+      int nl = colour_kernels(h->prm.dim, h->lv[level].N, c);
       cudaError_t e = cudaErrorNotSupported;
       if (h->prm.smoother == SIPG_SMOOTHER_CLAMPED) e = clamped_fused<T>(h, level, c, b, x, s);
       if (e == cudaErrorNotSupported) e = launch_full_colour<T>(h, level, c, b, x, s, &nl);
@@ -109,7 +128,7 @@ cudaError_t launch_smooth_step(const sipg_handle* h, int level, int reverse, con
     const int c = reverse ? nc - 1 - i : i;
     cudaError_t e = launch_smooth_colour<T>(h, level, c, b, x, s);
     if (e != cudaSuccess) return e;
-    *launches += 2;
+    *launches += colour_kernels(h->prm.dim, h->lv[level].N, c);
   }
   return cudaSuccess;
 }
