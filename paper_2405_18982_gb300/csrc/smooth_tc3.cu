@@ -451,6 +451,9 @@ cudaError_t launch_tc3(const sipg_handle* h, int level, int colour, const float*
     return cudaErrorNotSupported;
   const PatchGrid g = make_grid(3, h->lv[level].N, colour);
   if (g.n_int >= (1LL << 31)) return cudaErrorNotSupported;
+  // degree 7 only: with p = 2k < 14 the 16-wide operand tiles are mostly
+  // padding, and the FP32 kernel is faster (GB300, 32^3 colour 0: k = 5
+  // 60.8 against 39.4 us, k = 6 77.5 against 66.8 us; k = 7 97.3 against 109)
   switch (h->n) {
     case 8: return launch_tc3_impl<8>(h, level, colour, b, x, g, s);
     default: return cudaErrorNotSupported;
