@@ -703,8 +703,16 @@ def c4_records(torch, reps=2):
     torch.cuda.empty_cache()
 
     shapes = inputs.ragged_problems(4)
-    bt = SIPGBatch([Params(dim=2, degree=k, log2_cells=L, n_levels=L, vcycle_precision=SIPG_FP32, use_graphs=1)
-                    for L, k in shapes])
+    mk = lambda: SIPGBatch([Params(dim=2, degree=k, log2_cells=L, n_levels=L, vcycle_precision=SIPG_FP32,
+                                   use_graphs=1) for L, k in shapes])
+    bt = mk()
+    old = os.environ.get("SIPG_BATCH_FUSED")
+    os.environ["SIPG_BATCH_FUSED"] = "1"
+    bf = mk()      # the fused path: one cooperative launch per smoothing stage across members
+    if old is None:
+        del os.environ["SIPG_BATCH_FUSED"]
+    else:
+        os.environ["SIPG_BATCH_FUSED"] = old
     bs, xs = [], []
     for i, m in enumerate(bt.members):
         f = torch.from_numpy(inputs.normal(1000 + i, m.ndofs())).to("cuda").view(1, -1)
@@ -714,19 +722,23 @@ def c4_records(torch, reps=2):
         xs.append(torch.zeros_like(bb))
     total = sum(m.ndofs() for m in bt.members)
 
-    def batched():
+    def batched(b_=bt):
         for xx in xs:
             xx.zero_()
-        return bt.solve(bs, xs, rtol=1e-10, maxit=100)
+        return b_.solve(bs, xs, rtol=1e-10, maxit=100)
 
     def sequential():
         return [m.solve(bb, xx, rtol=1e-10, maxit=100, zero_start=True) for m, bb, xx in zip(bt.members, bs, xs)]
 
     ms_b, infos = timed(batched)
+    ms_f, infos_f = timed(lambda: batched(bf))
     ms_s, _ = timed(sequential)
+    bf.close()
     its = [i.iterations for i in infos]
     c4b = {"workload": "64 ragged 2D problems, L in 5..9, k in 2..6 (seed 4), mixed FCG to 1e-10",
            "total_dofs": total, "batched_ms_per_solve": round(ms_b, 3),
+           "fused_stages_ms_per_solve": round(ms_f, 3),
+           "fused_worst_rel_residual": max(i.rel_residual for i in infos_f),
            "sequential_ms_per_solve": round(ms_s, 3), "batched_MDoF_per_s": round(total / ms_b / 1e3, 1),
            "iterations_min_max": [min(its), max(its)], "worst_rel_residual": max(i.rel_residual for i in infos)}
     bt.close()
@@ -736,88 +748,13 @@ def c4_records(torch, reps=2):
 
 
 def run_batched(args):
-    """--mode ragged: 64 independent 2D problems (2^L x 2^L cells, L uniform in
-    5..9, degree uniform in 2..6, seeded), one mixed-precision batched solve to
-    1e-10 per step, next to the same members solved one after another.
-    --mode multirhs: 3D Q4 on 32^3 cells with 32 N(0,1) right-hand sides
-    (seeds 100..131) in one solve, next to one right-hand side alone."""
+    """--mode ragged / multirhs: the C4b / C4a records of c4_records (with
+    --steps timed solves after one warm-up)."""
     import torch
     import paper_2405_18982_gb300 as pkg
-    from paper_2405_18982_gb300 import SIPG, SIPG_FP32, Params, SIPGBatch, inputs
     pkg.load(pkg.build())
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-    def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(args.steps):
-            out = fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps, out
-
-    if args.mode == "ragged":
-        shapes = inputs.ragged_problems(4)
-        bt = SIPGBatch([Params(dim=2, degree=k, log2_cells=L, n_levels=L, vcycle_precision=SIPG_FP32,
-                               use_graphs=1) for L, k in shapes])
-        # f ~ N(0,1) per DoF, b = M f (the load vector of the nodal source)
-        bs, xs = [], []
-        for i, m in enumerate(bt.members):
-            f = torch.from_numpy(inputs.normal(1000 + i, m.ndofs())).to("cuda").view(1, -1)
-            b = torch.zeros_like(f)
-            m.rhs(f, b)
-            bs.append(b)
-            xs.append(torch.zeros_like(b))
-        total = sum(m.ndofs() for m in bt.members)
-
-        def batched():
-            for x in xs:
-                x.zero_()
-            return bt.solve(bs, xs, rtol=1e-10, maxit=100)
-
-        def sequential():
-            for x in xs:
-                x.zero_()
-            return [m.solve(b, x, rtol=1e-10, maxit=100) for m, b, x in zip(bt.members, bs, xs)]
-
-        ms_b, infos = timed(batched)
-        ms_s, _ = timed(sequential)
-        its = [i.iterations for i in infos]
-        print(json.dumps({"mode": "ragged", "problems": len(shapes), "total_dofs": total,
-                          "batched_ms_per_solve": round(ms_b, 3), "sequential_ms_per_solve": round(ms_s, 3),
-                          "batched_MDoF_per_s": round(total / ms_b / 1e3, 1),
-                          "iterations_min_max": [min(its), max(its)],
-                          "worst_rel_residual": max(i.rel_residual for i in infos),
-                          "shapes_L_k": shapes}))
-        return
-
-    nrhs = 32
-    s = SIPG(Params(dim=3, degree=4, log2_cells=5, n_levels=5, vcycle_precision=SIPG_FP32, nrhs=nrhs,
-                    use_graphs=1))
-    one = SIPG(Params(dim=3, degree=4, log2_cells=5, n_levels=5, vcycle_precision=SIPG_FP32, use_graphs=1))
-    nd = s.ndofs()
-    b = torch.from_numpy(inputs.normal_columns(list(range(100, 100 + nrhs)), nd)).to("cuda")
-    x = torch.zeros_like(b)
-    b1 = b[:1].contiguous()
-    x1 = torch.zeros_like(b1)
-
-    def multi():
-        x.zero_()
-        return s.solve(b, x, rtol=1e-10, maxit=100)
-
-    def single():
-        x1.zero_()
-        return one.solve(b1, x1, rtol=1e-10, maxit=100)
-
-    ms_m, inf = timed(multi)
-    ms_1, inf1 = timed(single)
-    print(json.dumps({"mode": "multirhs", "nrhs": nrhs, "ndofs_per_rhs": nd,
-                      "ms_per_solve": round(ms_m, 3), "MDoF_per_s": round(nd * nrhs / ms_m / 1e3, 1),
-                      "iterations": inf.iterations, "rel_residual": inf.rel_residual,
-                      "single_rhs_ms_per_solve": round(ms_1, 3),
-                      "single_MDoF_per_s": round(nd / ms_1 / 1e3, 1), "single_iterations": inf1.iterations}))
+    c4a, c4b = c4_records(torch, reps=max(1, args.steps))
+    print(json.dumps({"mode": args.mode, **(c4b if args.mode == "ragged" else c4a)}))
 
 
 # ----------------------------------------------------------------- throughput sweep

@@ -293,14 +293,29 @@ const char* sipg_batch_last_error(const sipg_batch* b);
 int sipg_batch_count(const sipg_batch* b);
 /* Member i (owned by the batch): use it for sipg_ndofs, sipg_rhs, ... */
 sipg_handle* sipg_batch_member(sipg_batch* b, int i);
-/* Sum of the members' workspaces (each 256-byte aligned inside). */
+/* Sum of the members' workspaces (each 256-byte aligned inside); with
+ * SIPG_BATCH_FUSED=1 and a batch of 2D problems with the FP32 V-cycle, one
+ * right-hand side each, degrees 2..6, a Dirichlet-kernel smoother and the
+ * 2 x 2 coarsest level, also the plan of the batched smoothing stages
+ * (sipg_batch_solve). */
 size_t sipg_batch_workspace_bytes(const sipg_batch* b);
 /* Bind one caller-owned buffer for all members (runs every member's setup). */
 sipg_status sipg_batch_bind_workspace(sipg_batch* b, void* dev_ptr, size_t bytes, void* stream);
 /* b[i], x[i]: device vectors of member i (host arrays of count pointers);
  * x[i] holds the initial guess on entry.  infos: NULL or count entries.
  * Returns the first member failure (sipg_batch_last_error names it).
- * Synchronises the internal streams. */
+ * Synchronises the internal streams.  Batches of 2D FP32 problems (see
+ * sipg_batch_workspace_bytes) run the flexible CG of all members in lockstep
+ * with one V-cycle of the whole batch per iteration: every smoothing step of a
+ * level is one cooperative launch over all members that have that level (all
+ * colours, bounded grid barriers between them), the per-member work (zeroing,
+ * residual and restriction, coarse solve, prolongation, Krylov updates) runs
+ * on the members' streams, and each iteration is one CUDA graph; every
+ * member's final true residual is verified (restarting that member alone if
+ * it drifted).  That fused path is selected by SIPG_BATCH_FUSED=1 in the
+ * environment at sipg_batch_create; by default every member runs on its own
+ * stream with its own V-cycles and CUDA graph (faster on GB300: the members'
+ * kernels overlap across members and levels). */
 sipg_status sipg_batch_solve(sipg_batch* b, const double* const* bvecs, double* const* xvecs, double rtol,
                              int maxit, sipg_info* infos, void* stream);
 

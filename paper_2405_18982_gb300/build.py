@@ -23,7 +23,7 @@ LIB = os.path.join(OUT_DIR, "libsipg.so")
 STAMP = os.path.join(OUT_DIR, "libsipg.machine")
 # the colour-pass instantiation units are the slowest: they go first
 SOURCES = (sorted(f for f in os.listdir(CSRC) if f.startswith("smooth_i_") and f.endswith(".cu")) +
-           ["smooth_tc3.cu", "apply.cu", "setup.cu", "transfer.cu", "smoother.cu", "smooth_full.cu", "api.cu",
+           ["smooth_tc3.cu", "smooth_batch2.cu", "apply.cu", "setup.cu", "transfer.cu", "smoother.cu", "smooth_full.cu", "api.cu",
             "krylov.cu", "noalloc.cu"])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -177,7 +177,8 @@ sipg_status iteration_body(sipg_handle* h, double* x, cudaStream_t s) {
 
 // Capture one iteration body as a CUDA graph (on the internal stream).
 sipg_status ensure_graph(sipg_handle* h, double* x) {
-  if (h->iter_exec && h->g_x == x) return SIPG_OK;
+  // (the tolerance is a kernel argument of the captured convergence test)
+  if (h->iter_exec && h->g_x == x && h->g_rtol2 == h->rtol2) return SIPG_OK;
   if (h->iter_exec) {
     cudaGraphExecDestroy(h->iter_exec);
     h->iter_exec = nullptr;
@@ -201,6 +202,7 @@ sipg_status ensure_graph(sipg_handle* h, double* x) {
   h->graph_launches = h->launches - before;
   h->launches = before;
   h->g_x = x;
+  h->g_rtol2 = h->rtol2;
   return SIPG_OK;
 }
 
@@ -1241,6 +1243,16 @@ struct sipg_batch {
   std::vector<cudaEvent_t> done;
   cudaEvent_t start = nullptr;
   std::string err;
+  // fused path (2D FP32 batches): batched smoothing stages, one CUDA graph per
+  // FCG iteration of the whole batch
+  bool fused = false;
+  size_t off_plan = 0;
+  BatchPlan2* plan = nullptr;
+  cudaStream_t gs = nullptr;                         // capture / launch stream
+  std::vector<cudaEvent_t> fork;                     // capture-time fork and join events
+  cudaGraphExec_t g_first = nullptr, g_iter = nullptr;
+  std::vector<double*> g_x;                          // solution vectors the graphs were captured with
+  double g_rtol2 = -1.0;
 };
 
 sipg_status sipg_batch_create(const sipg_params* params, int count, sipg_batch** out) {
@@ -1264,6 +1276,15 @@ sipg_status sipg_batch_create(const sipg_params* params, int count, sipg_batch**
     bt->off.push_back(off);
     off += align256(sipg_workspace_bytes(h));
   }
+  // the fused path (batched smoothing stages) is opt-in: measured on GB300 it
+  // is slower than the members on their own streams, whose kernels overlap
+  // across members and levels
+  bt->fused = false;
+  if (const char* env = getenv("SIPG_BATCH_FUSED")) bt->fused = atoi(env) != 0 && batch2_supported(bt->hs);
+  if (bt->fused) {
+    bt->off_plan = off;
+    off += align256(batch2_plan_bytes(bt->hs));
+  }
   bt->ws_bytes = off;
   *out = bt;
   return SIPG_OK;
@@ -1271,6 +1292,11 @@ sipg_status sipg_batch_create(const sipg_params* params, int count, sipg_batch**
 
 void sipg_batch_destroy(sipg_batch* bt) {
   if (!bt) return;
+  if (bt->g_first) cudaGraphExecDestroy(bt->g_first);
+  if (bt->g_iter) cudaGraphExecDestroy(bt->g_iter);
+  for (auto e : bt->fork) cudaEventDestroy(e);
+  if (bt->gs) cudaStreamDestroy(bt->gs);
+  if (bt->plan) batch2_plan_free(bt->plan);
   for (auto* h : bt->hs) sipg_destroy(h);
   for (auto s : bt->streams) cudaStreamDestroy(s);
   for (auto e : bt->done) cudaEventDestroy(e);
@@ -1319,7 +1345,268 @@ sipg_status sipg_batch_bind_workspace(sipg_batch* bt, void* dev_ptr, size_t byte
       return SIPG_ECUDA;
     }
   }
+  if (bt->fused && !bt->plan) {
+    // the members' level constants are on the host now: build the batched
+    // smoothing plan in the batch workspace
+    cudaError_t e = batch2_plan_build(bt->hs, static_cast<char*>(dev_ptr) + bt->off_plan, &bt->plan);
+    if (e != cudaSuccess) {
+      bt->err = std::string("batched smoothing plan: ") + cudaGetErrorString(e);
+      return SIPG_ECUDA;
+    }
+    if (cudaStreamCreateWithFlags(&bt->gs, cudaStreamNonBlocking) != cudaSuccess) {
+      bt->err = "stream creation failed";
+      return SIPG_ECUDA;
+    }
+  }
   return SIPG_OK;
+}
+
+// ---------------------------------------------------------- fused ragged batch
+// (CUDA failures here name the batch: BATCH_CHECK records the message in the
+// batch and returns SIPG_ECUDA)
+#define BATCH_CHECK(expr, where)                                                       \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      bt->err = std::string(where) + ": " + cudaGetErrorString(e_);                  \
+      return SIPG_ECUDA;                                                             \
+    }                                                                                \
+  } while (0)
+// Fork the member streams off `s` (every member stream waits for s) and join
+// them back (s waits for every member stream); captured into the batch graphs
+// as dependency edges.
+sipg_status batch_fork(sipg_batch* bt, cudaStream_t s, int slot) {
+  cudaEvent_t e = bt->fork[slot];
+  BATCH_CHECK(cudaEventRecord(e, s), "fork record");
+  for (auto ms : bt->streams) BATCH_CHECK(cudaStreamWaitEvent(ms, e, 0), "fork wait");
+  return SIPG_OK;
+}
+sipg_status batch_join(sipg_batch* bt, cudaStream_t s) {
+  for (size_t i = 0; i < bt->streams.size(); ++i) {
+    BATCH_CHECK(cudaEventRecord(bt->done[i], bt->streams[i]), "join record");
+    BATCH_CHECK(cudaStreamWaitEvent(s, bt->done[i], 0), "join wait");
+  }
+  return SIPG_OK;
+}
+
+// One FP32 V-cycle of every member (finest-level buffers bL -> xL), level by
+// level: per-member work (zeroing, residual and restriction, coarse solve,
+// prolongation) on the member streams, every smoothing step of a level as
+// one batched cooperative launch on s.
+sipg_status batch_vcycle(sipg_batch* bt, cudaStream_t s, int& slot) {
+  const int levels = batch2_levels(bt->plan);
+  const size_t nm = bt->hs.size();
+  auto bvec = [&](sipg_handle* h, int l) -> float* {
+    return l == h->L ? reinterpret_cast<float*>(h->ws + h->off_bL) : reinterpret_cast<float*>(h->vb(l));
+  };
+  auto xvec = [&](sipg_handle* h, int l) -> float* {
+    return l == h->L ? reinterpret_cast<float*>(h->ws + h->off_xL) : reinterpret_cast<float*>(h->vx(l));
+  };
+  sipg_status st;
+  for (int l = levels - 1; l >= 1; --l) {
+    if ((st = batch_fork(bt, s, slot++))) return st;
+    for (size_t i = 0; i < nm; ++i) {
+      sipg_handle* h = bt->hs[i];
+      if (l > h->L) continue;
+      BATCH_CHECK(cudaMemsetAsync(xvec(h, l), 0, h->lv[l].ndofs * sizeof(float), bt->streams[i]), "memset");
+    }
+    if ((st = batch_join(bt, s))) return st;
+    BATCH_CHECK(batch2_step(bt->plan, l, 0, s), "batched smoothing");
+    if ((st = batch_fork(bt, s, slot++))) return st;
+    for (size_t i = 0; i < nm; ++i) {
+      sipg_handle* h = bt->hs[i];
+      if (l > h->L) continue;
+      float* r = reinterpret_cast<float*>(h->vr(l));
+      BATCH_CHECK(launch_apply<float>(h, l, APPLY_RESIDUAL, bvec(h, l), xvec(h, l), r, bt->streams[i]), "residual");
+      BATCH_CHECK(launch_restrict<float>(h, l, r, bvec(h, l - 1), bt->streams[i]), "restrict");
+      if (l == 1) BATCH_CHECK(launch_coarse_solve<float>(h, bvec(h, 0), xvec(h, 0), bt->streams[i]), "coarse solve");
+    }
+  }
+  for (int l = 1; l < levels; ++l) {
+    if (l > 1 && (st = batch_fork(bt, s, slot++))) return st;
+    for (size_t i = 0; i < nm; ++i) {
+      sipg_handle* h = bt->hs[i];
+      if (l > h->L) continue;
+      BATCH_CHECK(launch_prolongate_add<float>(h, l, xvec(h, l - 1), xvec(h, l), bt->streams[i]), "prolongate");
+    }
+    if ((st = batch_join(bt, s))) return st;
+    BATCH_CHECK(batch2_step(bt->plan, l, 1, s), "batched smoothing");
+  }
+  return SIPG_OK;
+}
+
+// One FCG iteration of every member: V-cycle (batched), then per member the
+// preconditioned-direction update, q = A p, the step and the scalars' copy to
+// the host.  first: z_0 = B r_0 from the FP64 residual, p_0 = z_0.
+sipg_status batch_iteration(sipg_batch* bt, const std::vector<double*>& xs, bool first, cudaStream_t s) {
+  int slot = 0;
+  sipg_status st;
+  const size_t nm = bt->hs.size();
+  if (first) {
+    if ((st = batch_fork(bt, s, slot++))) return st;
+    for (size_t i = 0; i < nm; ++i) {
+      sipg_handle* h = bt->hs[i];
+      BATCH_CHECK(convert_d2f(h->kr(), reinterpret_cast<float*>(h->ws + h->off_bL), h->lv[h->L].ndofs, bt->streams[i]),
+                 "convert");
+    }
+    if ((st = batch_join(bt, s))) return st;
+  }
+  if ((st = batch_vcycle(bt, s, slot))) return st;
+  if ((st = batch_fork(bt, s, slot++))) return st;
+  for (size_t i = 0; i < nm; ++i) {
+    sipg_handle* h = bt->hs[i];
+    cudaStream_t ms = bt->streams[i];
+    BATCH_CHECK(krylov_after_precond(h, first ? 1 : 0, h->kr(), h->ws + h->off_xL, 1, ms), "precond post");
+    BATCH_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, h->kp(), h->kq(), ms), "apply");
+    BATCH_CHECK(krylov_after_apply(h, ms), "pq");
+    BATCH_CHECK(krylov_update_xr(h, xs[i], h->ws + h->off_bL, 1, ms), "update");
+    BATCH_CHECK(cudaMemcpyAsync(h->pinned, h->scalars(), sizeof(KrylovScalars), cudaMemcpyDeviceToHost, ms),
+               "scalars D2H");
+  }
+  return batch_join(bt, s);
+}
+
+sipg_status batch_capture(sipg_batch* bt, const std::vector<double*>& xs, bool first, cudaGraphExec_t* out) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  BATCH_CHECK(cudaStreamBeginCapture(bt->gs, cudaStreamCaptureModeThreadLocal), "begin capture");
+  sipg_status st = batch_iteration(bt, xs, first, bt->gs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(bt->gs, &graph);
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return bt->err = "end capture", SIPG_ECUDA;
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bt->err = "graph instantiate", SIPG_ECUDA;
+  return SIPG_OK;
+}
+
+// Lockstep flexible CG over all members with the batched V-cycle: the true
+// residual per member, then iterations of the whole batch (two CUDA graphs:
+// the first iteration and the others) until no member is active or maxit;
+// members whose recursively updated residual converged keep their x (the
+// Krylov kernels skip inactive columns).  The final true residual of each
+// member is verified by the per-member path (which restarts a member whose
+// residual drifted).
+sipg_status batch_solve_fused(sipg_batch* bt, const double* const* b, double* const* x, double rtol, int maxit,
+                              sipg_info* infos, cudaStream_t cs) {
+  const size_t nm = bt->hs.size();
+  std::vector<double*> xs(x, x + nm);
+  if (bt->fork.size() < 64) {
+    const size_t old = bt->fork.size();
+    bt->fork.resize(64);
+    for (size_t i = old; i < bt->fork.size(); ++i)
+      if (cudaEventCreateWithFlags(&bt->fork[i], cudaEventDisableTiming) != cudaSuccess)
+        return bt->err = "event creation failed", SIPG_ECUDA;
+  }
+  const double rtol2 = rtol * rtol;
+  if (!bt->g_iter || bt->g_x != xs || bt->g_rtol2 != rtol2) {
+    for (auto* h : bt->hs) h->rtol2 = rtol2;
+    sipg_status st = batch_capture(bt, xs, true, &bt->g_first);
+    if (!st) st = batch_capture(bt, xs, false, &bt->g_iter);
+    if (st) return st;
+    bt->g_x = xs;
+    bt->g_rtol2 = rtol2;
+  }
+  // initial true residuals and norms, on the member streams after cs
+  if (cudaEventRecord(bt->start, cs) != cudaSuccess) return SIPG_ECUDA;
+  std::vector<FcgRun> runs(nm);
+  for (size_t i = 0; i < nm; ++i) {
+    sipg_handle* h = bt->hs[i];
+    h->rtol2 = rtol2;
+    if (cudaStreamWaitEvent(bt->streams[i], bt->start, 0) != cudaSuccess) return SIPG_ECUDA;
+    runs[i].h = h;
+    runs[i].b = b[i];
+    runs[i].x = x[i];
+    runs[i].s = bt->streams[i];
+    runs[i].maxit = maxit;
+    runs[i].info = infos ? &infos[i] : nullptr;
+    sipg_status st = launch_true_residual(runs[i]);
+    if (st) return bt->err = "member " + std::to_string(i) + ": " + h->err, st;
+  }
+  for (size_t i = 0; i < nm; ++i)
+    if (cudaStreamSynchronize(bt->streams[i]) != cudaSuccess) return bt->err = "sync", SIPG_ECUDA;
+  for (size_t i = 0; i < nm; ++i) {
+    runs[i].pending = false;
+    runs[i].hist.push_back(sqrt(bt->hs[i]->pinned[0].rr));
+  }
+  auto any_active = [&]() {
+    for (auto* h : bt->hs)
+      if (h->pinned[0].active && !h->pinned[0].breakdown) return true;
+    return false;
+  };
+  // the graphs wait for the member streams' initial work through gs
+  for (size_t i = 0; i < nm; ++i) {
+    if (cudaEventRecord(bt->done[i], bt->streams[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(bt->gs, bt->done[i], 0) != cudaSuccess)
+      return SIPG_ECUDA;
+  }
+  int it = 0;
+  std::vector<bool> was_active(nm);
+  while (any_active() && it < maxit) {
+    for (size_t i = 0; i < nm; ++i) was_active[i] = bt->hs[i]->pinned[0].active && !bt->hs[i]->pinned[0].breakdown;
+    if (cudaGraphLaunch(it == 0 ? bt->g_first : bt->g_iter, bt->gs) != cudaSuccess)
+      return bt->err = "graph launch", SIPG_ECUDA;
+    if (cudaStreamSynchronize(bt->gs) != cudaSuccess) return bt->err = "sync", SIPG_ECUDA;
+    ++it;
+    for (size_t i = 0; i < nm; ++i) {
+      if (!was_active[i]) continue;
+      runs[i].it = it;
+      runs[i].hist.push_back(sqrt(bt->hs[i]->pinned[0].rr));
+    }
+  }
+  {
+    int status = 0;
+    if (cudaMemcpy(&status, batch2_status(bt->plan), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return SIPG_ECUDA;
+    if (status != 0) {
+      cudaMemset(batch2_status(bt->plan) - 2, 0, 3 * sizeof(int));
+      bt->err = "a bounded grid-barrier wait of the batched smoother timed out";
+      return SIPG_ETIMEOUT;
+    }
+  }
+  // verify: the per-member state machine from its VERIFY phase (true
+  // residual; a restart if it drifted; the members' own V-cycles then)
+  for (size_t i = 0; i < nm; ++i) {
+    runs[i].phase = FcgRun::VERIFY;
+    runs[i].restarts = -1;
+    if (cudaStreamWaitEvent(bt->streams[i], bt->start, 0) != cudaSuccess) return SIPG_ECUDA;
+    sipg_status st = launch_true_residual(runs[i]);
+    if (st) return st;
+  }
+  sipg_status st = SIPG_OK;
+  for (;;) {
+    bool any = false;
+    for (auto& r : runs) {
+      if (!r.pending) continue;
+      any = true;
+      if (cudaStreamSynchronize(r.s) != cudaSuccess) return SIPG_ECUDA;
+    }
+    if (!any) break;
+    for (auto& r : runs) {
+      if (!r.pending) continue;
+      st = advance(r);
+      if (st) return st;
+    }
+  }
+  sipg_status worst = SIPG_OK;
+  for (size_t i = 0; i < nm; ++i) {
+    sipg_status si = finish(runs[i]);
+    if (si != SIPG_OK && worst == SIPG_OK) {
+      worst = si;
+      bt->err = "member " + std::to_string(i) + ": " + bt->hs[i]->err;
+    }
+  }
+  for (size_t i = 0; i < nm; ++i) {
+    cudaEventRecord(bt->done[i], bt->streams[i]);
+    cudaStreamWaitEvent(cs, bt->done[i], 0);
+  }
+  return worst;
 }
 
 sipg_status sipg_batch_solve(sipg_batch* bt, const double* const* b, double* const* x, double rtol, int maxit,
@@ -1337,6 +1624,7 @@ sipg_status sipg_batch_solve(sipg_batch* bt, const double* const* b, double* con
     }
   }
   cudaStream_t cs = S(stream);
+  if (bt->plan) return batch_solve_fused(bt, b, x, rtol, maxit, infos, cs);
   if (cudaEventRecord(bt->start, cs) != cudaSuccess) return SIPG_ECUDA;
   std::vector<FcgRun> runs(n);
   for (size_t i = 0; i < n; ++i) {

@@ -140,6 +140,7 @@ struct sipg_handle {
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   double* g_x = nullptr;
+  double g_rtol2 = -1.0;  // the tolerance the captured iteration was recorded with
   uint64_t graph_launches = 0;               // kernels inside one graph launch
 
   LevelConst<double>* c64(int l) const { return reinterpret_cast<LevelConst<double>*>(ws + off_const64) + l; }
@@ -233,6 +234,15 @@ int colour_kernels(int dim, int N, int colour);
 // sweeps on the tensor cores (TF32); cudaErrorNotSupported where that kernel
 // does not apply (the caller then launches the FP32 kernel).
 cudaError_t launch_tc3(const sipg_handle* h, int level, int colour, const float* b, float* x, cudaStream_t s);
+// Ragged 2D batches: batched smoothing stages (smooth_batch2.cu).
+struct BatchPlan2;
+bool batch2_supported(const std::vector<sipg_handle*>& hs);
+size_t batch2_plan_bytes(const std::vector<sipg_handle*>& hs);
+cudaError_t batch2_plan_build(const std::vector<sipg_handle*>& hs, char* dev, BatchPlan2** out);
+void batch2_plan_free(BatchPlan2* p);
+int batch2_levels(const BatchPlan2* p);
+cudaError_t batch2_step(const BatchPlan2* p, int level, int reverse, cudaStream_t s);
+int* batch2_status(const BatchPlan2* p);
 cudaError_t launch_tc_selftest(const sipg_handle* h, const float* A, const float* B, float* D, cudaStream_t s);
 // smem_opt_in, then the kernel's resident CTAs per SM at that launch shape on
 // the current device (cached per kernel, device and shape).

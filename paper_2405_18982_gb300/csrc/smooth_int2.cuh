@@ -40,15 +40,21 @@ struct I2 {
   static constexpr int VW = run_vw<NN, T>();
 };
 
-template <int NN, typename T, bool BND>
-__global__ void __launch_bounds__(I2<NN, T, BND>::THREADS)
-    smooth_int2_kernel(const __grid_constant__ SmoothOps<I2<NN, T, BND>::PO, 2 * NN, T, I2<NN, T, BND>::NT> ops,
-                       int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
-                       PatchGrid grid) {
+// Patches pbase + slot (slot < PPC, TPP threads each) of one colour; every
+// thread of the CTA calls this (it holds CTA barriers), threads past the PPC
+// slots only take part in the barriers.  smem_raw: the kernel's dynamic
+// shared memory (the boundary operator sets are copied there).  NC: x is read
+// through the read-only path, valid when no other CTA writes what this launch
+// reads (one colour per launch); launches that run several colours with grid
+// barriers between them use coherent loads.
+template <int NN, typename T, bool BND, bool NC>
+__device__ __forceinline__ void int2_body(const SmoothOps<I2<NN, T, BND>::PO, 2 * NN, T, I2<NN, T, BND>::NT>& ops,
+                                          unsigned char* smem_raw, long long pbase, int colour,
+                                          const T* __restrict__ b, T* x, int N, int consistent,
+                                          const PatchGrid& grid) {
   using C = I2<NN, T, BND>;
   using Ops = Ops1D<C::PO, 2 * NN, T>;
   constexpr int P = C::P, PO = C::PO, OFF = C::OFF, TPP = C::TPP, PPC = C::PPC, SA = C::SA, ND = NN * NN;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const Ops* sops = reinterpret_cast<const Ops*>(smem_raw);
   if (BND) {
     const int* src = reinterpret_cast<const int*>(&ops);
@@ -58,14 +64,11 @@ __global__ void __launch_bounds__(I2<NN, T, BND>::THREADS)
   const int tid = threadIdx.x;
   const int lane = tid % TPP;
   const int pl = tid / TPP;
-  T* RA = reinterpret_cast<T*>(smem_raw + C::PREFIX) + (size_t)pl * C::PS;
+  T* RA = reinterpret_cast<T*>(smem_raw + C::PREFIX) + (size_t)(pl < PPC ? pl : 0) * C::PS;
   T* RB = RA + C::RA;
-  const long long col = (long long)blockIdx.y * ndofs;
-  b += col;
-  x += col;
   const long long npatch = BND ? grid.n_bnd : grid.n_int;
-  const long long pidx = (long long)blockIdx.x * PPC + pl;
-  const bool valid = pidx < npatch;
+  const long long pidx = pbase + pl;
+  const bool valid = pl < PPC && pidx < npatch;
   int m[3] = {0, 0, 0};
   patch_index<2, BND>(grid, valid ? pidx : 0, m);
   int v[2], ty[2];
@@ -108,14 +111,14 @@ __global__ void __launch_bounds__(I2<NN, T, BND>::THREADS)
         ld = side ? exhi[1] : exlo[1];
       }
       if (ld) {
-        i3_ldrun<NN, C::VW, T>(xb + off, &vin[q][0]);
-        i3_ldrun<NN, C::VW, T>(xb + off + ND, &vin[q][NN]);
+        i3_ldrun<NN, C::VW, T, NC>(xb + off, &vin[q][0]);
+        i3_ldrun<NN, C::VW, T, NC>(xb + off + ND, &vin[q][NN]);
       } else {
 #pragma unroll
         for (int c = 0; c < P; ++c) vin[q][c] = T(0);
       }
-      hl[q][0] = (main && exlo[0]) ? __ldg(xb + off - ND + (NN - 1)) : T(0);
-      hl[q][1] = (main && exhi[0]) ? __ldg(xb + off + 2 * ND) : T(0);
+      hl[q][0] = (main && exlo[0]) ? ld_elem<NC>(xb + off - ND + (NN - 1)) : T(0);
+      hl[q][1] = (main && exhi[0]) ? ld_elem<NC>(xb + off + 2 * ND) : T(0);
     }
 #pragma unroll
     for (int q = 0; q < R1; ++q) {
@@ -204,6 +207,17 @@ __global__ void __launch_bounds__(I2<NN, T, BND>::THREADS)
       if (in) gx[((r1 + OFF) / NN) * cs1 + ((r1 + OFF) % NN) * NN] = xo[r1] + u[r1];
     }
   }
+}
+
+template <int NN, typename T, bool BND>
+__global__ void __launch_bounds__(I2<NN, T, BND>::THREADS)
+    smooth_int2_kernel(const __grid_constant__ SmoothOps<I2<NN, T, BND>::PO, 2 * NN, T, I2<NN, T, BND>::NT> ops,
+                       int colour, const T* __restrict__ b, T* x, int N, int consistent, long long ndofs,
+                       PatchGrid grid) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long col = (long long)blockIdx.y * ndofs;
+  int2_body<NN, T, BND, true>(ops, smem_raw, (long long)blockIdx.x * I2<NN, T, BND>::PPC, colour, b + col, x + col,
+                              N, consistent, grid);
 }
 
 template <int NN, typename T, bool BND>

@@ -100,6 +100,7 @@ def test_batch_host_only_calls_without_gpu(lib):
         assert m and lib.sipg_ndofs(m, L - 1) == (1 << L) ** 2 * (k + 1) ** 2
         total += (lib.sipg_workspace_bytes(m) + 255) // 256 * 256
     assert not lib.sipg_batch_member(b, 3)
+    # (the fused path is opt-in: by default the members' workspaces only)
     assert lib.sipg_batch_workspace_bytes(b) == total
     # solving before binding is rejected
     ptrs = (ctypes.c_void_p * 3)(16, 16, 16)

@@ -1,7 +1,11 @@
 """Ragged batch of independent problems (sipg_batch_*): every member's
 solution against the oracle's exact global fast-diagonalisation solve and
 against the same problem solved alone; the full 64-problem 2D batch (2^L x 2^L
-cells, L in 5..9, degree 2..6) as the benchmark runs it."""
+cells, L in 5..9, degree 2..6) as the benchmark runs it.  With
+SIPG_BATCH_FUSED=1 all-2D FP32 batches take the fused path (one cooperative
+launch per smoothing stage across the members, one CUDA graph per FCG
+iteration of the batch): its members match the oracle's exact solves and the
+same batch on the per-member path, including the full 64-problem batch."""
 import numpy as np
 import pytest
 
@@ -96,3 +100,61 @@ def test_ragged64_full_batch(ragged64):
         u = GlobalFD(d, k, 1 << L).solve(host(bs[i]))
         err = np.linalg.norm(host(xs[i]) - u) / np.linalg.norm(u)
         assert err < 1e-8, (i, L, k, err)
+
+
+FUSED = [(2, 3, 2), (2, 5, 6), (2, 4, 3), (2, 6, 2), (2, 2, 5), (2, 5, 4), (2, 3, 6), (2, 4, 4)]
+
+
+@pytest.mark.parametrize("rtol", [1e-10, 1e-12])
+def test_fused_batch_matches_direct_and_per_member_path(monkeypatch, rtol):
+    import torch
+    monkeypatch.setenv("SIPG_BATCH_FUSED", "1")
+    bt = SIPGBatch(_params(FUSED, SIPG_FP32))
+    bs = _rhs(bt, 340)
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = bt.solve(bs, xs, rtol=rtol, maxit=100)
+    monkeypatch.setenv("SIPG_BATCH_FUSED", "0")
+    ref = SIPGBatch(_params(FUSED, SIPG_FP32))
+    ys = [torch.zeros_like(b) for b in bs]
+    rinfos = ref.solve(bs, ys, rtol=rtol, maxit=100)
+    for (d, L, k), b, x, y, inf, rinf in zip(FUSED, bs, xs, ys, infos, rinfos):
+        assert inf.status == 0 and inf.rel_residual <= rtol
+        u = GlobalFD(d, k, 1 << L).solve(host(b))
+        err = np.linalg.norm(host(x) - u) / np.linalg.norm(u)
+        assert err < (1e-8 if rtol >= 1e-10 else 1e-9), (L, k, err)
+        # the same preconditioner (FP32 colour passes of the same
+        # arithmetic), so the same iterations and nearly the same iterates
+        assert abs(inf.iterations - rinf.iterations) <= 1
+        assert np.linalg.norm(host(x) - host(y)) <= 1e-8 * np.linalg.norm(host(y))
+
+
+def test_fused_batch_repeat_is_deterministic(monkeypatch):
+    import torch
+    monkeypatch.setenv("SIPG_BATCH_FUSED", "1")
+    bt = SIPGBatch(_params(FUSED, SIPG_FP32))
+    bs = _rhs(bt, 350)
+    xs = [torch.zeros_like(b) for b in bs]
+    first = bt.solve(bs, xs, rtol=1e-10)
+    ys = [torch.zeros_like(b) for b in bs]
+    second = bt.solve(bs, ys, rtol=1e-10)
+    for a, b_, i1, i2 in zip(xs, ys, first, second):
+        assert torch.equal(a, b_) and i1.iterations == i2.iterations
+    # from the converged solutions: no iteration
+    again = bt.solve(bs, xs, rtol=1e-10)
+    assert all(i.iterations == 0 and i.status == 0 for i in again)
+
+
+def test_fused_ragged64_matches_per_member_path(monkeypatch, ragged64):
+    import torch
+    shapes, ref = ragged64
+    monkeypatch.setenv("SIPG_BATCH_FUSED", "1")
+    bt = SIPGBatch(_params(shapes, SIPG_FP32))
+    bs = _rhs(bt, 1100)
+    xs = [torch.zeros_like(b) for b in bs]
+    ys = [torch.zeros_like(b) for b in bs]
+    infos = bt.solve(bs, xs, rtol=1e-10, maxit=100)
+    rinfos = ref.solve(bs, ys, rtol=1e-10, maxit=100)
+    for x, y, i, r in zip(xs, ys, infos, rinfos):
+        assert i.status == 0 and i.rel_residual <= 1e-10
+        assert abs(i.iterations - r.iterations) <= 1
+        assert np.linalg.norm(host(x) - host(y)) <= 1e-8 * np.linalg.norm(host(y))
