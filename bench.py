@@ -820,7 +820,9 @@ def run_table2(args):
     the device: 3D unit cube, f = 1, 2^L cells per direction down to 2^3 on
     the coarsest level, GMRES to 1e-8 preconditioned from the right by one
     V-cycle whose smoother uses the Dirichlet-kernel residual; nu (Sec. 3.3),
-    steps and time to solution with the FP64 and the FP32 V-cycle, the
+    steps and time to solution with the FP64 and the FP32 V-cycle (each
+    restart cycle one graph launch on the device, and step by step from the
+    host), the
     consistent residual, the full kernel (Table 1's setting) and the clamped
     kernel (Table 2 right; also with GMRES preconditioned from the left, the
     reading that reproduces that column) beside it, and the values printed
@@ -846,14 +848,20 @@ def run_table2(args):
                    "nu_table2": None if np.isnan(printed[L - 2, k - 2]) else float(printed[L - 2, k - 2])}
             row["nu_table1"] = None if np.isnan(printed1[L - 2, k - 2]) else float(printed1[L - 2, k - 2])
             row["nu_table2_clamped"] = None if np.isnan(printed_c[L - 2, k - 2]) else float(printed_c[L - 2, k - 2])
-            for tag, prec, sm, left in (("fp64", SIPG_FP64, SIPG_SMOOTHER_PAPER, False),
-                                        ("mixed", SIPG_FP32, SIPG_SMOOTHER_PAPER, False),
-                                        ("consistent_mixed", SIPG_FP32, SIPG_SMOOTHER_CONSISTENT, False),
-                                        ("full_mixed", SIPG_FP32, SIPG_SMOOTHER_FULL, False),
-                                        ("clamped_mixed", SIPG_FP32, SIPG_SMOOTHER_CLAMPED, False),
-                                        # left preconditioning needs a fixed linear V-cycle: FP64
-                                        ("clamped_fp64_left", SIPG_FP64, SIPG_SMOOTHER_CLAMPED, True)):
-                s = SIPG(Params(dim=3, degree=k, log2_cells=L, n_levels=L, vcycle_precision=prec, smoother=sm))
+            # graphs = 1: every GMRES restart cycle is one graph launch on the
+            # device; the *_hoststeps rows drive each step from the host
+            for tag, prec, sm, left, graphs in (
+                    ("fp64", SIPG_FP64, SIPG_SMOOTHER_PAPER, False, 1),
+                    ("mixed", SIPG_FP32, SIPG_SMOOTHER_PAPER, False, 1),
+                    ("fp64_hoststeps", SIPG_FP64, SIPG_SMOOTHER_PAPER, False, 0),
+                    ("mixed_hoststeps", SIPG_FP32, SIPG_SMOOTHER_PAPER, False, 0),
+                    ("consistent_mixed", SIPG_FP32, SIPG_SMOOTHER_CONSISTENT, False, 1),
+                    ("full_mixed", SIPG_FP32, SIPG_SMOOTHER_FULL, False, 1),
+                    ("clamped_mixed", SIPG_FP32, SIPG_SMOOTHER_CLAMPED, False, 1),
+                    # left preconditioning needs a fixed linear V-cycle: FP64
+                    ("clamped_fp64_left", SIPG_FP64, SIPG_SMOOTHER_CLAMPED, True, 1)):
+                s = SIPG(Params(dim=3, degree=k, log2_cells=L, n_levels=L, vcycle_precision=prec, smoother=sm,
+                                use_graphs=graphs))
                 f = torch.ones(1, s.ndofs(), dtype=torch.float64, device="cuda")
                 b = torch.zeros_like(f)
                 s.rhs(f, b)

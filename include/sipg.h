@@ -124,7 +124,7 @@ typedef struct {
   int vcycle_precision;  /* sipg_precision                                               */
   int smoother;          /* sipg_smoother                                                */
   int nrhs;              /* >= 1 right-hand sides solved together                        */
-  int use_graphs;        /* != 0: capture one Krylov iteration in a CUDA graph           */
+  int use_graphs;        /* != 0: FCG iterations and GMRES cycles as CUDA graphs         */
 } sipg_params;
 
 typedef struct {
@@ -255,8 +255,13 @@ size_t sipg_gmres_workspace_bytes(const sipg_handle* h, int restart);
  * with any other argument.  info->iterations counts GMRES steps (V-cycles);
  * info->nu is computed from the history as for sipg_solve.  Returns
  * SIPG_ENOCONV after maxit steps, SIPG_EBREAKDOWN on a non-finite scalar.
- * Synchronises stream (after every step: the Hessenberg matrix is kept on
- * the host). */
+ * Synchronises stream.  With params.use_graphs = 1 each restart cycle runs
+ * on the device as one CUDA graph launch (a conditional while node over the
+ * Arnoldi step; Hessenberg matrix, rotations and stopping test in device
+ * memory), so the host synchronises once per cycle; the graph is recorded
+ * on the first call for a given work pointer, restart length and side of
+ * preconditioning.  Otherwise the host drives every step and synchronises
+ * after each. */
 sipg_status sipg_gmres_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
                              int restart, void* work, size_t work_bytes, sipg_info* info, void* stream);
 /* The same GMRES preconditioned from the left: Arnoldi on B A, the residual

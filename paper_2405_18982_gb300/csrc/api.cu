@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <set>
 #include <tuple>
@@ -425,9 +426,9 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
 // Caller-owned workspace of sipg_gmres_solve: Arnoldi vectors V_0..V_m and
 // preconditioned vectors Z_0..Z_{m-1} (finest level, FP64, each 256-byte
 // aligned), reduction partials for m+1 simultaneous dot products, m+1
-// device scalars.
+// device scalars, the device state of one restart cycle.
 struct GmresLayout {
-  size_t vec = 0, off_z = 0, off_part = 0, off_dev = 0, total = 0;
+  size_t vec = 0, off_z = 0, off_part = 0, off_dev = 0, off_state = 0, total = 0;
 };
 
 GmresLayout gmres_layout(const sipg_handle* h, int m) {
@@ -436,7 +437,8 @@ GmresLayout gmres_layout(const sipg_handle* h, int m) {
   g.off_z = (size_t)(m + 1) * g.vec;
   g.off_part = g.off_z + (size_t)m * g.vec;
   g.off_dev = g.off_part + align256(sizeof(double) * (size_t)(m + 1) * h->n_partials);
-  g.total = g.off_dev + align256(sizeof(double) * (size_t)(m + 1));
+  g.off_state = g.off_dev + align256(sizeof(double) * (size_t)(m + 1));
+  g.total = g.off_state + align256(sizeof(GmresCycleState));
   return g;
 }
 
@@ -492,6 +494,133 @@ struct GmresVectors {
   }
 };
 
+// One Arnoldi step of a device-resident cycle (j read from st by every
+// kernel).  Right: z_j = B v_j into Z_j, w = A z_j; left: w = B A v_j.  The
+// finest-level Krylov vectors of the handle (unused by GMRES otherwise) are
+// the scratch: T0, T1 = w, T2.  Then classical Gram-Schmidt applied twice,
+// ||w||^2, the rotations on the device, v_{j+1} = w / ||w||.
+sipg_status gmres_step_body(sipg_handle* h, const GmresVectors& g, int m, GmresCycleState* st,
+                            cudaGraphConditionalHandle cond, cudaStream_t s) {
+  double* T0 = h->kp();
+  double* T1 = h->kq();
+  double* T2 = h->kz();
+  const long long n = g.n;
+  const bool f32 = h->prm.vcycle_precision == SIPG_FP32;
+  float* bL = reinterpret_cast<float*>(h->ws + h->off_bL);
+  float* xL = reinterpret_cast<float*>(h->ws + h->off_xL);
+  sipg_status st_ = SIPG_OK;
+  if (!g.left) {
+    if (f32) {
+      SIPG_CHECK(gmres_gather(h, g.V, g.ld, st, bL, true, n, s), "gather");
+      st_ = vcycle_T<float>(h, bL, xL, s);
+      if (st_) return st_;
+      SIPG_CHECK(gmres_put(h, xL, true, g.Z, g.ld, st, T0, n, s), "put");
+    } else {
+      SIPG_CHECK(gmres_gather(h, g.V, g.ld, st, T0, false, n, s), "gather");
+      st_ = vcycle_T<double>(h, T0, T2, s);
+      if (st_) return st_;
+      SIPG_CHECK(gmres_put(h, T2, false, g.Z, g.ld, st, nullptr, n, s), "put");
+    }
+    SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, f32 ? T0 : T2, T1, s), "apply");
+    h->launches += 1;
+  } else {
+    SIPG_CHECK(gmres_gather(h, g.V, g.ld, st, T0, false, n, s), "gather");
+    SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, T0, T2, s), "apply");
+    h->launches += 1;
+    st_ = gmres_precond(h, T2, T1, s);
+    if (st_) return st_;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    double* c = pass ? st->hc2 : st->hc1;
+    SIPG_CHECK(gmres_mdot_dev(h, g.V, g.ld, st, m, T1, n, g.part, c, s), "dot");
+    SIPG_CHECK(gmres_maxpy_dev(h, T1, g.V, g.ld, st, c, n, s), "axpy");
+  }
+  SIPG_CHECK(gmres_mdot(h, T1, g.ld, 1, T1, n, g.part, &st->nrm, s), "dot");
+  SIPG_CHECK(gmres_rotate(h, st, cond, s), "rotate");
+  SIPG_CHECK(gmres_next(h, T1, g.V, g.ld, st, n, s), "next");
+  return SIPG_OK;
+}
+
+// The cycle graph: one conditional while node (condition 1 at launch) whose
+// body, recorded by stream capture, is one Arnoldi step; the rotation kernel
+// sets the condition.  Recorded once per workspace, restart length and side.
+sipg_status gmres_ensure_graph(sipg_handle* h, const GmresVectors& g, int m, GmresCycleState* st) {
+  const char* work = reinterpret_cast<const char*>(g.V);
+  if (h->gm_exec && h->gm_work == work && h->gm_m == m && h->gm_left == g.left) return SIPG_OK;
+  if (h->gm_exec) {
+    cudaGraphExecDestroy(h->gm_exec);
+    h->gm_exec = nullptr;
+  }
+  if (!h->gstream) SIPG_CHECK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking), "stream");
+  if (!h->ev_a) SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming), "event");
+  if (!h->ev_b) SIPG_CHECK(cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming), "event");
+  cudaGraph_t graph = nullptr;
+  SIPG_CHECK(cudaGraphCreate(&graph, 0), "graph create");
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(h, e, "conditional node");
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const uint64_t before = h->launches;
+  e = cudaStreamBeginCaptureToGraph(h->gstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(h, e, "begin capture");
+  }
+  sipg_status st_ = gmres_step_body(h, g, m, st, cond, h->gstream);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(h->gstream, &captured);
+  if (st_ || e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    h->launches = before;
+    if (st_) return st_;
+    return cuda_fail(h, e, "end capture");
+  }
+  e = cudaGraphInstantiate(&h->gm_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->gm_exec = nullptr;
+    h->launches = before;
+    return cuda_fail(h, e, "graph instantiate");
+  }
+  h->gm_launches = h->launches - before;
+  h->launches = before;
+  h->gm_work = work;
+  h->gm_m = m;
+  h->gm_left = g.left;
+  return SIPG_OK;
+}
+
+// One restart cycle on the device: clear the state, run the cycle graph,
+// read the state back (the only host synchronisation of the cycle).
+sipg_status gmres_device_cycle(sipg_handle* h, const GmresVectors& g, int m, GmresCycleState* st, double beta,
+                               double thr, int budget, GmresCycleState* out) {
+  sipg_status r = gmres_ensure_graph(h, g, m, st);
+  if (r) return r;
+  cudaStream_t s = g.s;
+  SIPG_CHECK(gmres_cycle_setup(h, st, beta, thr, budget, s), "cycle setup");
+  SIPG_CHECK(cudaEventRecord(h->ev_a, s), "event record");
+  SIPG_CHECK(cudaStreamWaitEvent(h->gstream, h->ev_a, 0), "stream wait");
+  SIPG_CHECK(cudaGraphLaunch(h->gm_exec, h->gstream), "graph launch");
+  SIPG_CHECK(cudaEventRecord(h->ev_b, h->gstream), "event record");
+  SIPG_CHECK(cudaStreamWaitEvent(s, h->ev_b, 0), "stream wait");
+  SIPG_CHECK(cudaMemcpyAsync(out, st, sizeof(GmresCycleState), cudaMemcpyDeviceToHost, s), "D2H");
+  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  h->launches += h->gm_launches * (uint64_t)std::max(out->runs, 0);
+  return SIPG_OK;
+}
+
 sipg_status gmres_run(sipg_handle* h, const double* b, double* x, double rtol, int maxit, int m, char* work,
                       sipg_info* info, cudaStream_t s, bool left = false) {
   const GmresLayout lay = gmres_layout(h, m);
@@ -519,6 +648,12 @@ sipg_status gmres_run(sipg_handle* h, const double* b, double* x, double rtol, i
   // Hessenberg matrix (row-major, (m+1) x m), rotations, right-hand side
   std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), y(m), hc(m + 1), tmp(m + 1);
   auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  // with CUDA graphs on, every cycle runs on the device (one graph launch,
+  // one host synchronisation per cycle); else the host drives every step
+  const bool on_device = h->prm.use_graphs != 0;
+  GmresCycleState* st_dev = reinterpret_cast<GmresCycleState*>(work + lay.off_state);
+  std::unique_ptr<GmresCycleState> hs;
+  if (on_device) hs.reset(new GmresCycleState());
   while (!conv && result == SIPG_OK && steps < maxit) {
     const int mc = std::min(m, maxit - steps);
     SIPG_CHECK(gmres_scale(h, g.v(0), 1.0 / beta, g.n, s), "scale");
@@ -526,7 +661,19 @@ sipg_status gmres_run(sipg_handle* h, const double* b, double* x, double rtol, i
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int j = 0;  // completed steps of this cycle
-    while (j < mc) {
+    if (on_device) {
+      st = gmres_device_cycle(h, g, m, st_dev, beta, rtol * bnorm, mc, hs.get());
+      if (st) return st;
+      j = std::min(std::max(hs->j, 0), mc);
+      for (int i = 0; i < j; ++i) hist.push_back(hs->hist[i]);
+      steps += j;
+      if (hs->brk) result = SIPG_EBREAKDOWN;
+      for (int i = 0; i <= j; ++i) {
+        gv[i] = hs->g[i];
+        for (int q = 0; q < j; ++q) Hat(i, q) = hs->H[i * SIPG_GMRES_MAXM + q];
+      }
+    }
+    while (!on_device && j < mc) {
       if (left) {  // v_{j+1} = B A v_j (A v_j in Z_j)
         SIPG_CHECK(launch_apply<double>(h, h->L, APPLY_Y, nullptr, g.v(j), g.z(j), s), "apply");
         h->launches += 1;
@@ -830,6 +977,7 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
 void sipg_destroy(sipg_handle* h) {
   if (!h) return;
   if (h->iter_exec) cudaGraphExecDestroy(h->iter_exec);
+  if (h->gm_exec) cudaGraphExecDestroy(h->gm_exec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->ev_a) cudaEventDestroy(h->ev_a);
   if (h->ev_b) cudaEventDestroy(h->ev_b);
@@ -859,6 +1007,10 @@ sipg_status sipg_bind_workspace(sipg_handle* h, void* dev_ptr, size_t bytes, voi
   if (h->iter_exec) {
     cudaGraphExecDestroy(h->iter_exec);
     h->iter_exec = nullptr;
+  }
+  if (h->gm_exec) {
+    cudaGraphExecDestroy(h->gm_exec);
+    h->gm_exec = nullptr;
   }
   h->ws = reinterpret_cast<char*>(dev_ptr);
   h->bound = true;

@@ -221,8 +221,27 @@ __global__ void __launch_bounds__(RB) mdot_partial_kernel(const double* V, long 
   if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
 }
 
+// partials of <V_i, w> for every i <= *lim in one launch (one block per
+// partial, vectors in turn): the same element-to-partial mapping as
+// mdot_partial_kernel with gridDim.x blocks, so the sums are the same
+__global__ void __launch_bounds__(RB) mdot_multi_partial_kernel(const double* V, long long ld, const double* w,
+                                                                long long n, double* partials, const int* lim) {
+  const int cnt = *lim + 1;
+  const long long stride = (long long)gridDim.x * RB;
+  for (int q = 0; q < cnt; ++q) {
+    const double* v = V + (long long)q * ld;
+    double acc[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) acc[0] = fma(v[i], w[i], acc[0]);
+    block_sum<1>(acc);
+    if (threadIdx.x == 0) partials[(long long)q * gridDim.x + blockIdx.x] = acc[0];
+    __syncthreads();  // block_sum's shared slots are reused by the next vector
+  }
+}
+
 // out[i] = the nb partials of vector i = blockIdx.x summed in a fixed order
-__global__ void __launch_bounds__(RB) mdot_finalize_kernel(const double* partials, int nb, double* out) {
+__global__ void __launch_bounds__(RB) mdot_finalize_kernel(const double* partials, int nb, double* out,
+                                                           const int* lim) {
+  if (lim && (int)blockIdx.x > *lim) return;
   double acc[1] = {0.0};
   for (int i = threadIdx.x; i < nb; i += RB) acc[0] += partials[(long long)blockIdx.x * nb + i];
   block_sum<1>(acc);
@@ -234,9 +253,11 @@ struct GmresCoef {
 };
 
 // w += sign * sum_{q < cnt} c_q V_q with c from device memory (cdev) or from
-// the parameter block (cdev == nullptr)
+// the parameter block (cdev == nullptr); with cnt_dev, cnt = *cnt_dev + 1
 __global__ void __launch_bounds__(RB) maxpy_kernel(double* w, const double* V, long long ld, int cnt,
-                                                   const double* cdev, GmresCoef cpar, double sign, long long n) {
+                                                   const double* cdev, GmresCoef cpar, double sign, long long n,
+                                                   const int* cnt_dev) {
+  if (cnt_dev) cnt = *cnt_dev + 1;
   const long long stride = (long long)gridDim.x * RB;
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
     double acc = 0.0;
@@ -250,6 +271,110 @@ __global__ void __launch_bounds__(RB) scale_kernel(double* w, double a, long lon
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) w[i] *= a;
 }
 
+// ------------------------------------------- GMRES cycle on the device
+__global__ void __launch_bounds__(RB) gmres_setup_kernel(GmresCycleState* st, double beta, double thr,
+                                                         int budget) {
+  constexpr int M = SIPG_GMRES_MAXM;
+  for (int i = threadIdx.x; i < (M + 1) * M; i += RB) st->H[i] = 0.0;
+  for (int i = threadIdx.x; i <= M; i += RB) {
+    st->g[i] = 0.0;
+    st->hc1[i] = 0.0;
+    st->hc2[i] = 0.0;
+    if (i < M) {
+      st->cs[i] = 0.0;
+      st->sn[i] = 0.0;
+      st->hist[i] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->j = 0;
+    st->budget = budget;
+    st->conv = 0;
+    st->brk = 0;
+    st->runs = 0;
+    st->thr = thr;
+    st->nrm = 0.0;
+    st->hn = 0.0;
+    st->g[0] = beta;
+  }
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(RB) gmres_gather_kernel(const double* V, long long ld, const GmresCycleState* st,
+                                                          TO* out, long long n) {
+  const double* v = V + (long long)st->j * ld;
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) out[i] = (TO)v[i];
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(RB) gmres_put_kernel(const TI* in, double* Z, long long ld,
+                                                       const GmresCycleState* st, double* copy, long long n) {
+  double* z = Z + (long long)st->j * ld;
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+    const double v = (double)in[i];
+    z[i] = v;
+    if (copy) copy[i] = v;
+  }
+}
+
+// One thread: the step's Hessenberg column and rotations, the same
+// arithmetic in the same order as the host loop of gmres_run.  Every path
+// ends in exactly one cudaGraphSetConditional, and the loop stops at the
+// latest after `budget` bodies (runs), whatever the flags say.
+__global__ void gmres_rotate_kernel(GmresCycleState* st, cudaGraphConditionalHandle cond) {
+  constexpr int M = SIPG_GMRES_MAXM;
+  unsigned int more = 0;
+  st->runs += 1;
+  const int j = st->j;
+  if (!st->conv && !st->brk && j < st->budget && j < M && st->runs <= st->budget) {
+    double* H = st->H;
+    const double hn = sqrt(st->nrm);
+    bool finite = isfinite(hn);
+    for (int i = 0; i <= j; ++i) finite = finite && isfinite(st->hc1[i] + st->hc2[i]);
+    if (!finite) {
+      st->brk = 1;
+    } else {
+      for (int i = 0; i <= j; ++i) H[i * M + j] = st->hc1[i] + st->hc2[i];
+      H[(j + 1) * M + j] = hn;
+      st->hn = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * M + j], c = H[(i + 1) * M + j];
+        H[i * M + j] = st->cs[i] * a + st->sn[i] * c;
+        H[(i + 1) * M + j] = -st->sn[i] * a + st->cs[i] * c;
+      }
+      const double den = hypot(H[j * M + j], H[(j + 1) * M + j]);
+      if (!(den > 0.0)) {
+        st->brk = 1;
+      } else {
+        st->cs[j] = H[j * M + j] / den;
+        st->sn[j] = H[(j + 1) * M + j] / den;
+        H[j * M + j] = den;
+        H[(j + 1) * M + j] = 0.0;
+        st->g[j + 1] = -st->sn[j] * st->g[j];
+        st->g[j] = st->cs[j] * st->g[j];
+        st->hist[j] = fabs(st->g[j + 1]);
+        st->j = j + 1;
+        if (fabs(st->g[j + 1]) <= st->thr || hn == 0.0) st->conv = 1;
+        more = (!st->conv && st->j < st->budget) ? 1u : 0u;
+      }
+    }
+  }
+  cudaGraphSetConditional(cond, more);
+}
+
+__global__ void __launch_bounds__(RB) gmres_next_kernel(const double* w, double* V, long long ld,
+                                                        const GmresCycleState* st, long long n) {
+  if (st->brk) return;
+  double* v = V + (long long)st->j * ld;
+  const double hn = st->hn;
+  const double a = hn > 0.0 ? 1.0 / hn : 1.0;
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) v[i] = w[i] * a;
+}
+
 }  // namespace
 
 static inline long long fine_n(const sipg_handle* h) { return (long long)h->lv[h->L].ndofs; }
@@ -259,7 +384,7 @@ cudaError_t gmres_mdot(sipg_handle* h, const double* V, long long ld, int cnt, c
   if (cnt < 1 || cnt > SIPG_GMRES_MAXM + 1) return cudaErrorInvalidValue;
   dim3 grid(h->n_partials, cnt);
   mdot_partial_kernel<<<grid, RB, 0, s>>>(V, ld, w, n, partials);
-  mdot_finalize_kernel<<<cnt, RB, 0, s>>>(partials, h->n_partials, out);
+  mdot_finalize_kernel<<<cnt, RB, 0, s>>>(partials, h->n_partials, out, nullptr);
   h->launches += 2;
   return cudaGetLastError();
 }
@@ -270,7 +395,7 @@ cudaError_t gmres_maxpy(sipg_handle* h, double* w, const double* V, long long ld
   GmresCoef cp;
   for (int q = 0; q <= SIPG_GMRES_MAXM; ++q) cp.c[q] = (!cdev && q < cnt) ? chost[q] : 0.0;
   const int blocks = std::min(ceil_div(n, RB), 64 * h->num_sms);
-  maxpy_kernel<<<blocks, RB, 0, s>>>(w, V, ld, cnt, cdev, cp, sign, n);
+  maxpy_kernel<<<blocks, RB, 0, s>>>(w, V, ld, cnt, cdev, cp, sign, n, nullptr);
   h->launches += 1;
   return cudaGetLastError();
 }
@@ -278,6 +403,67 @@ cudaError_t gmres_maxpy(sipg_handle* h, double* w, const double* V, long long ld
 cudaError_t gmres_scale(sipg_handle* h, double* w, double a, long long n, cudaStream_t s) {
   const int blocks = std::min(ceil_div(n, RB), 64 * h->num_sms);
   scale_kernel<<<blocks, RB, 0, s>>>(w, a, n);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+static inline int vec_blocks(const sipg_handle* h, long long n) {
+  return (int)std::min<long long>(ceil_div(n, RB), 64LL * h->num_sms);
+}
+
+cudaError_t gmres_cycle_setup(sipg_handle* h, GmresCycleState* st, double beta, double thr, int budget,
+                              cudaStream_t s) {
+  gmres_setup_kernel<<<1, RB, 0, s>>>(st, beta, thr, budget);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_gather(sipg_handle* h, const double* V, long long ld, const GmresCycleState* st, void* out,
+                         bool out_float, long long n, cudaStream_t s) {
+  if (out_float)
+    gmres_gather_kernel<float><<<vec_blocks(h, n), RB, 0, s>>>(V, ld, st, static_cast<float*>(out), n);
+  else
+    gmres_gather_kernel<double><<<vec_blocks(h, n), RB, 0, s>>>(V, ld, st, static_cast<double*>(out), n);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_put(sipg_handle* h, const void* in, bool in_float, double* Z, long long ld,
+                      const GmresCycleState* st, double* copy, long long n, cudaStream_t s) {
+  if (in_float)
+    gmres_put_kernel<float><<<vec_blocks(h, n), RB, 0, s>>>(static_cast<const float*>(in), Z, ld, st, copy, n);
+  else
+    gmres_put_kernel<double><<<vec_blocks(h, n), RB, 0, s>>>(static_cast<const double*>(in), Z, ld, st, copy, n);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_mdot_dev(sipg_handle* h, const double* V, long long ld, const GmresCycleState* st, int m,
+                           const double* w, long long n, double* partials, double* out, cudaStream_t s) {
+  if (m < 1 || m > SIPG_GMRES_MAXM) return cudaErrorInvalidValue;
+  mdot_multi_partial_kernel<<<h->n_partials, RB, 0, s>>>(V, ld, w, n, partials, &st->j);
+  mdot_finalize_kernel<<<m + 1, RB, 0, s>>>(partials, h->n_partials, out, &st->j);
+  h->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_maxpy_dev(sipg_handle* h, double* w, const double* V, long long ld, const GmresCycleState* st,
+                            const double* c, long long n, cudaStream_t s) {
+  GmresCoef cp{};
+  maxpy_kernel<<<vec_blocks(h, n), RB, 0, s>>>(w, V, ld, 0, c, cp, -1.0, n, &st->j);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_rotate(sipg_handle* h, GmresCycleState* st, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  gmres_rotate_kernel<<<1, 1, 0, s>>>(st, cond);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_next(sipg_handle* h, const double* w, double* V, long long ld, const GmresCycleState* st,
+                       long long n, cudaStream_t s) {
+  gmres_next_kernel<<<vec_blocks(h, n), RB, 0, s>>>(w, V, ld, st, n);
   h->launches += 1;
   return cudaGetLastError();
 }

@@ -76,6 +76,29 @@ struct KrylovScalars {
   int breakdown;   // set when a scalar is non-finite or <p,q> <= 0
 };
 
+// Device-resident state of one GMRES restart cycle (Sec. 3.3), read and
+// written by the step kernels so that a whole cycle runs as one graph launch
+// without host round trips: the Hessenberg matrix (row-major, row stride
+// SIPG_GMRES_MAXM), the plane rotations, the rotated right-hand side g, the
+// Gram-Schmidt coefficients of the two passes, the squared norm of the new
+// direction and |g_{j+1}| after every step.
+struct GmresCycleState {
+  int j;       // completed steps of this cycle
+  int budget;  // steps allowed in this cycle
+  int conv;    // |g_j| <= thr, or an exactly zero new direction
+  int brk;     // a non-finite scalar or a zero rotation denominator
+  int runs;    // step bodies executed (bounds the loop on its own)
+  int pad_[3];
+  double thr;  // rtol ||b|| (left preconditioning: rtol ||B b||)
+  double nrm;  // ||w||^2 of the current step's new direction
+  double hn;   // ||w||: the subdiagonal entry of the current column
+  double pad2_;
+  double H[(SIPG_GMRES_MAXM + 1) * SIPG_GMRES_MAXM];
+  double cs[SIPG_GMRES_MAXM], sn[SIPG_GMRES_MAXM], g[SIPG_GMRES_MAXM + 1];
+  double hc1[SIPG_GMRES_MAXM + 1], hc2[SIPG_GMRES_MAXM + 1];
+  double hist[SIPG_GMRES_MAXM];
+};
+
 struct LevelInfo {
   int N;
   size_t ndofs;    // one rhs
@@ -142,6 +165,14 @@ struct sipg_handle {
   double* g_x = nullptr;
   double g_rtol2 = -1.0;  // the tolerance the captured iteration was recorded with
   uint64_t graph_launches = 0;               // kernels inside one graph launch
+  // CUDA graph of one GMRES restart cycle: a conditional while node whose
+  // body is one Arnoldi step, recorded for one workspace, restart length
+  // and side of preconditioning
+  cudaGraphExec_t gm_exec = nullptr;
+  const char* gm_work = nullptr;
+  int gm_m = 0;
+  bool gm_left = false;
+  uint64_t gm_launches = 0;                  // kernels in one step body
 
   LevelConst<double>* c64(int l) const { return reinterpret_cast<LevelConst<double>*>(ws + off_const64) + l; }
   LevelConst<float>* c32(int l) const { return reinterpret_cast<LevelConst<float>*>(ws + off_const32) + l; }
@@ -219,6 +250,29 @@ cudaError_t gmres_mdot(sipg_handle* h, const double* V, long long ld, int cnt, c
 cudaError_t gmres_maxpy(sipg_handle* h, double* w, const double* V, long long ld, int cnt, const double* cdev,
                         const double* chost, double sign, long long n, cudaStream_t s);
 cudaError_t gmres_scale(sipg_handle* h, double* w, double a, long long n, cudaStream_t s);
+// Device-resident cycle (GmresCycleState st; j = st->j when the kernel runs):
+// setup: st cleared, g_0 = beta, thr and budget set; gather: out = V_j
+// (converted to float when out_float); put: Z_j = in (float or double
+// input) and, if copy is not null, copy = the same values; mdot_dev:
+// out[i] = <V_i, w> for i <= j (grid sized for m + 1 vectors); maxpy_dev:
+// w -= sum_{i <= j} c_i V_i; rotate: the new Hessenberg column from hc1 +
+// hc2 and sqrt(nrm), the earlier rotations, the new rotation, g, hist, the
+// stopping flags, j += 1, and the loop condition of the cycle graph set to
+// continue or stop; next: V_j = w / ||w|| (j already advanced; nothing after
+// a breakdown).
+cudaError_t gmres_cycle_setup(sipg_handle* h, GmresCycleState* st, double beta, double thr, int budget,
+                              cudaStream_t s);
+cudaError_t gmres_gather(sipg_handle* h, const double* V, long long ld, const GmresCycleState* st, void* out,
+                         bool out_float, long long n, cudaStream_t s);
+cudaError_t gmres_put(sipg_handle* h, const void* in, bool in_float, double* Z, long long ld,
+                      const GmresCycleState* st, double* copy, long long n, cudaStream_t s);
+cudaError_t gmres_mdot_dev(sipg_handle* h, const double* V, long long ld, const GmresCycleState* st, int m,
+                           const double* w, long long n, double* partials, double* out, cudaStream_t s);
+cudaError_t gmres_maxpy_dev(sipg_handle* h, double* w, const double* V, long long ld, const GmresCycleState* st,
+                            const double* c, long long n, cudaStream_t s);
+cudaError_t gmres_rotate(sipg_handle* h, GmresCycleState* st, cudaGraphConditionalHandle cond, cudaStream_t s);
+cudaError_t gmres_next(sipg_handle* h, const double* w, double* V, long long ld, const GmresCycleState* st,
+                       long long n, cudaStream_t s);
 cudaError_t convert_d2f(const double* a, float* b, size_t n, cudaStream_t s);
 cudaError_t convert_f2d(const float* a, double* b, size_t n, cudaStream_t s);
 cudaError_t copy_or_zero(void* dst, size_t bytes, cudaStream_t s);

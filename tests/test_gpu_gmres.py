@@ -34,16 +34,17 @@ def hierarchy(dim, k, N, nl, kappa=1.0, variant="consistent"):
     return _HIER[key]
 
 
+@pytest.mark.parametrize("graphs", [0, 1], ids=["host-steps", "device-cycles"])
 @pytest.mark.parametrize("variant", [0, 1, 2], ids=["consistent", "paper", "full"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_gmres_history_matches_oracle(case, variant):
+def test_gmres_history_matches_oracle(case, variant, graphs):
     # same V-cycle (FP64), same GMRES: the residual after every step agrees
     # with the oracle's (the device orthogonalises by classical Gram-Schmidt
     # applied twice, the oracle by modified Gram-Schmidt: equal in exact
-    # arithmetic)
+    # arithmetic); with graphs every restart cycle runs on the device
     dim, k, l2, nl = case
     N = 1 << l2
-    s = make(dim, k, l2, nl, kappa=1.1, smoother=variant)
+    s = make(dim, k, l2, nl, kappa=1.1, smoother=variant, graphs=graphs)
     H = hierarchy(dim, k, N, nl, kappa=1.1, variant=("consistent", "paper", "full")[variant])
     b = rhs_from_nodal(dim, k, N, inputs.normal(700, H.A.shape[0]))
     x_ref, h_ref = gmres(lambda v: H.A @ v, H.vcycle, b, rtol=1e-10, maxit=100, restart=30)
@@ -73,10 +74,11 @@ def test_gmres_solution_matches_exact(case, prec, variant):
     assert rel_inf(host(xd), u) < (1e-10 if prec == SIPG_FP64 else 1e-8)
 
 
-def test_gmres_restarts_and_warm_start():
+@pytest.mark.parametrize("graphs", [0, 1], ids=["host-steps", "device-cycles"])
+def test_gmres_restarts_and_warm_start(graphs):
     dim, k, l2, nl = 3, 3, 3, 2
     N = 1 << l2
-    s = make(dim, k, l2, nl, smoother=1)
+    s = make(dim, k, l2, nl, smoother=1, graphs=graphs)
     b = rhs_from_nodal(dim, k, N, inputs.normal(730, s.ndofs()))
     u = GlobalFD(dim, k, N).solve(b)
     xd = dev(np.zeros_like(b))
@@ -88,6 +90,40 @@ def test_gmres_restarts_and_warm_start():
     # warm start from the solution: converged before the first step
     info2 = s.gmres_solve(dev(b), xd, rtol=1e-10, maxit=10, restart=5)
     assert info2.iterations == 0 and info2.rel_residual <= 1e-10
+
+
+@pytest.mark.parametrize("prec,left", [(SIPG_FP64, False), (SIPG_FP32, False), (SIPG_FP64, True)],
+                         ids=["fp64-right", "mixed-right", "fp64-left"])
+def test_device_cycles_equal_host_steps(prec, left):
+    # the same GMRES driven step by step from the host and as one graph
+    # launch per restart cycle: same steps, histories and solutions up to
+    # rounding (the rotations run on the host in one and on the device in
+    # the other); short restarts and a step limit that ends inside a cycle
+    dim, k, l2, nl = 3, 3, 4, 3
+    N = 1 << l2
+    b = rhs_from_nodal(dim, k, N, inputs.normal(760, (N * (k + 1)) ** 3))
+    runs = {}
+    for graphs in (0, 1):
+        s = make(dim, k, l2, nl, prec=prec, smoother=0, graphs=graphs)
+        xd = dev(np.zeros_like(b))
+        info = s.gmres_solve(dev(b), xd, rtol=1e-11, maxit=100, restart=4, left=left)
+        x2 = dev(np.zeros_like(b))
+        info2 = s.gmres_solve(dev(b), x2, rtol=1e-11, maxit=7, restart=3, left=left, allow_noconv=True)
+        # a second solve reuses the recorded cycle graph
+        x3 = dev(np.zeros_like(b))
+        info3 = s.gmres_solve(dev(b), x3, rtol=1e-11, maxit=100, restart=4, left=left)
+        runs[graphs] = (info, host(xd), info2, host(x2), info3, host(x3))
+    (i0, x0, j0, y0, _, _), (i1, x1, j1, y1, k1, z1) = runs[0], runs[1]
+    assert i0.status == 0 and i1.status == 0 and i1.iterations == i0.iterations > 4
+    h0, h1 = np.array(i0.history), np.array(i1.history)
+    assert len(h0) == len(h1) and np.all(np.abs(h1 - h0) <= 1e-9 * h0 + 1e-14 * h0[0])
+    assert rel_inf(x1, x0) < 1e-10
+    assert j0.status == j1.status and j1.iterations == j0.iterations == 7
+    assert np.allclose(j1.history, j0.history, rtol=1e-9, atol=1e-14 * h0[0])
+    assert rel_inf(y1, y0) < 1e-10
+    assert k1.iterations == i1.iterations and np.array_equal(z1, x1)
+    u = GlobalFD(dim, k, N).solve(b)
+    assert rel_inf(x1, u) < (1e-9 if prec == SIPG_FP64 else 1e-8)
 
 
 def test_gmres_errors():
