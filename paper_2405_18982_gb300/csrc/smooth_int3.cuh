@@ -157,8 +157,9 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
       const int w = grid.hi[e] - grid.lo[e];
-      const int m = grid.lo[e] + q % w;
-      q /= w;
+      const int qn = div_width(q, grid.dmul[e], grid.dshift[e]);
+      const int m = grid.lo[e] + (q - qn * w);
+      q = qn;
       v[e] = ((colour >> e) & 1) ? 2 * m + 1 : 2 * m + 2;
     }
   }

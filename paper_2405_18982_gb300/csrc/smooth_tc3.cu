@@ -186,12 +186,13 @@ __global__ void __launch_bounds__(256, 3)
   for (long long pidx = blockIdx.x; pidx < grid.n_int; pidx += gridDim.x) {
     int v[3];
     {
-      long long q = pidx;
+      int q = (int)pidx;
 #pragma unroll
       for (int e = 0; e < 3; ++e) {
         const int w = grid.hi[e] - grid.lo[e];
-        const int m = grid.lo[e] + (int)(q % w);
-        q /= w;
+        const int qn = div_width(q, grid.dmul[e], grid.dshift[e]);
+        const int m = grid.lo[e] + (q - qn * w);
+        q = qn;
         v[e] = ((colour >> e) & 1) ? 2 * m + 1 : 2 * m + 2;
       }
     }

@@ -340,19 +340,32 @@ void make_ops(const LevelConst<T>& lc, int t, Ops1D<PO, P, T>& op) {
 // parity) or 2m+2 (even); interior box [lo, hi) in m.
 struct PatchGrid {
   int cnt[3], lo[3], hi[3];
+  // the interior-box widths w = hi - lo as divisions by multiplication
+  // (Granlund and Montgomery, "Division by invariant integers using
+  // multiplication", 1994, Thm. 4.2 with N = 31): q / w = umulhi(q, dmul) >>
+  // dshift for 0 <= q < 2^31; dmul = 0 marks w <= 1 (q / 1 = q)
+  unsigned int dmul[3];
+  int dshift[3];
   long long n_int, n_bnd;
 };
+
+__device__ __forceinline__ int div_width(int q, unsigned int dmul, int dshift) {
+  return dmul ? (int)(__umulhi((unsigned int)q, dmul) >> dshift) : q;
+}
 
 __device__ __forceinline__ int outside_map(int q, int lo, int hi) { return q < lo ? q : q - lo + hi; }
 
 template <int DIM, bool BND>
 __device__ __forceinline__ void patch_index(const PatchGrid& g, long long idx, int (&m)[3]) {
   if (!BND) {
-    long long q = idx;
+    // interior indices stay below 2^31: a colour with 2^31 interior patches
+    // would need more than 2^34 DoFs, beyond any device memory
+    int q = (int)idx;
     for (int e = 0; e < DIM; ++e) {
       const int w = g.hi[e] - g.lo[e];
-      m[e] = g.lo[e] + (int)(q % w);
-      q /= w;
+      const int qn = div_width(q, g.dmul[e], g.dshift[e]);
+      m[e] = g.lo[e] + (q - qn * w);
+      q = qn;
     }
     return;
   }
@@ -1040,6 +1053,13 @@ PatchGrid make_grid(int dim, int N, int colour) {
     }
     tot *= g.cnt[e] > 0 ? g.cnt[e] : 0;
     inner *= (g.hi[e] - g.lo[e]);
+    // multiplier ceil(2^(31 + l) / w) with 2^l >= w > 2^(l-1): exact for
+    // every dividend below 2^31 and below 2^32 itself
+    const long long w = g.hi[e] - g.lo[e];
+    int l = 0;
+    while ((1LL << l) < w) ++l;
+    g.dmul[e] = w > 1 ? (unsigned int)(((1ULL << (31 + l)) + (unsigned long long)w - 1) / (unsigned long long)w) : 0u;
+    g.dshift[e] = w > 1 ? l - 1 : 0;
   }
   if (tot <= 0) {
     g.n_int = g.n_bnd = 0;
