@@ -812,6 +812,7 @@ sipg_status tune_T(sipg_handle* h, cudaStream_t s) {
       cands.push_back({1, 1});
       cands.push_back({1, 2});
       cands.push_back({1, 3});
+      cands.push_back({1, 4});
     }
     if (h->fuse_small_levels) cands.push_back({0, 0});
     float best = 1e30f;
@@ -913,7 +914,7 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   if (const char* env = getenv("SIPG_AUTOTUNE")) h->autotune = atoi(env) != 0;
   if (const char* env = getenv("SIPG_TILE")) {
     const int t = atoi(env);
-    h->force_tile = (t >= 0 && t <= 3) ? t : 0;
+    h->force_tile = (t >= 0 && t <= 4) ? t : 0;
   }
   h->n = n;
   h->L = L;

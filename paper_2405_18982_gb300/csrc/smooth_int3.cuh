@@ -52,7 +52,8 @@ struct I3 {
   // at most 512 threads
   // (TILE = 1: half as many, for the autotuner; TILE = 2, 3: the default
   // tile with b and x on V_j loaded ahead of the sweeps that use them, at
-  // four and three CTAs per SM)
+  // four and three CTAs per SM; TILE = 4: tile 3 with the x and y sweeps on
+  // whole warps)
   static constexpr int ppc() {
     int k = (54 * 1024 - PREFIX) / (PS * (int)sizeof(T));
     if (k > 512 / TPP) k = 512 / TPP;
@@ -68,11 +69,16 @@ struct I3 {
     int m = by_smem < by_thr ? by_smem : by_thr;
     // boundary patches: longer lines need more registers; they run beside
     // the interior kernel
-    const int cap = BND ? 2 : (TILE == 1 ? 8 : (TILE == 3 ? 3 : 4));
+    const int cap = BND ? 2 : (TILE == 1 ? 8 : (TILE >= 3 ? 3 : 4));
     return m < 1 ? 1 : (m > cap ? cap : m);
   }
   static constexpr int MINB = minblocks();
   static constexpr bool PF = !BND && TILE >= 2;  // loads of b and x on V_j issued early
+  // TILE = 4: the x and y sweeps run on whole warps, WPP warps per patch, so
+  // that their rounds of lines do not straddle two patches in one warp
+  static constexpr int WPP = (THREADS / 32) / PPC;
+  static constexpr bool WP = !BND && TILE == 4 && WPP >= 1;
+  static constexpr int TPA = WP ? 32 * WPP : TPP;  // threads per patch in the x and y sweeps
   static constexpr int VW = run_vw<NN, T>();
 };
 
@@ -125,7 +131,7 @@ __device__ __forceinline__ void int3_dinv(const Ops1D<2 * NN - 2, 2 * NN, T>& o0
 // read-only (non-coherent) path, valid when no other CTA writes what this
 // launch reads (one colour per launch); the fused step, whose later colours
 // read what other CTAs wrote, uses coherent loads.
-template <int NN, typename T, bool BND, int PPC, bool NC, bool PF = false>
+template <int NN, typename T, bool BND, int PPC, bool NC, bool PF = false, int TILE = 0>
 __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT>& ops,
                                           const T* dinv, T* buf, long long pbase, int colour,
                                           const T* __restrict__ b, T* x, int N, int consistent,
@@ -175,16 +181,45 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
   const T* xb = x + ((long long)(v[0] - 1) + (long long)N * ((v[1] - 1) + (long long)N * (v[2] - 1))) * ND;
   const int cs1 = N * ND, cs2 = N * N * ND;  // cell strides in y and z (elements)
 
+  // the x and y sweeps' view: this thread's patch and line index there (the
+  // same as above unless the sweeps run on whole warps, WP)
+  using CT = I3<NN, T, BND, TILE>;
+  constexpr bool WP = CT::WP;
+  constexpr int TPA = CT::TPA;
+  int lA = lane;
+  bool vA = valid;
+  const T* xA = xb;
+  T* RAA = RA;
+  if constexpr (WP) {
+    const int wid = tid / 32;
+    const int pa = wid / CT::WPP;
+    lA = (wid % CT::WPP) * 32 + (tid % 32);
+    vA = pa < PPC && pbase + pa < npatch;
+    int q = vA ? (int)(pbase + pa) : 0;
+    int va[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int w = grid.hi[e] - grid.lo[e];
+      const int qn = div_width(q, grid.dmul[e], grid.dshift[e]);
+      const int m = grid.lo[e] + (q - qn * w);
+      q = qn;
+      va[e] = ((colour >> e) & 1) ? 2 * m + 1 : 2 * m + 2;
+    }
+    xA = x + ((long long)(va[0] - 1) + (long long)N * ((va[1] - 1) + (long long)N * (va[2] - 1))) * ND;
+    RAA = buf + (size_t)(pa < PPC ? pa : 0) * C::PS;
+  }
+  T* RBA = RAA + C::RA;
+
   // ------------------------------------------------------------------ x sweep
   // lines t < P^2: (a1, a2) = (t / P, t % P); then 4P halo lines (slot, j):
   // slot 0/1 = y faces below/above (j = a2), 2/3 = z faces (j = a1), M_x only
   constexpr int L1 = P * P + 4 * P;
-  constexpr int R1 = (L1 + TPP - 1) / TPP;
-  if (valid) {
+  constexpr int R1 = (L1 + TPA - 1) / TPA;
+  if (vA) {
     T vin[R1][P], hl[R1][2];
 #pragma unroll
     for (int q = 0; q < R1; ++q) {
-      const int t = lane + q * TPP;
+      const int t = lA + q * TPA;
       int off = 0;
       const bool act = t < L1, main = t < P * P;
       bool ld = main;
@@ -202,21 +237,21 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
         }
       }
       if (ld) {
-        i3_ldrun<NN, C::VW, T, NC>(xb + off, &vin[q][0]);
-        i3_ldrun<NN, C::VW, T, NC>(xb + off + ND, &vin[q][NN]);
+        i3_ldrun<NN, C::VW, T, NC>(xA + off, &vin[q][0]);
+        i3_ldrun<NN, C::VW, T, NC>(xA + off + ND, &vin[q][NN]);
       } else {
 #pragma unroll
         for (int c = 0; c < P; ++c) vin[q][c] = T(0);
       }
       // x halos of a main line: node n-1 of cell v0-2, node 0 of cell v0+1
-      hl[q][0] = (main && exlo[0]) ? ld_elem<NC>(xb + off - ND + (NN - 1)) : T(0);
-      hl[q][1] = (main && exhi[0]) ? ld_elem<NC>(xb + off + 2 * ND) : T(0);
+      hl[q][0] = (main && exlo[0]) ? ld_elem<NC>(xA + off - ND + (NN - 1)) : T(0);
+      hl[q][1] = (main && exhi[0]) ? ld_elem<NC>(xA + off + 2 * ND) : T(0);
     }
     i3_with_type<BND>(ty[0], [&](auto tc) {
       const Ops& ox = ops.t[decltype(tc)::value];
 #pragma unroll
       for (int q = 0; q < R1; ++q) {
-        const int t = lane + q * TPP;
+        const int t = lA + q * TPA;
         if (t >= L1) continue;
         // destination row: A/B[a1][a2][.] for main lines, halo[slot][j][.]
         const int dst = t < P * P ? SA1 * (t / P) + PO * (t % P)
@@ -224,11 +259,11 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
         T oa[PO];
         T(&vq)[P] = vin[q];
         mass_rows2<PO, P, NN, OFF, false>(ox, vq, oa);
-        i3_st_pairs<PO>(RA + dst, oa);
+        i3_st_pairs<PO>(RAA + dst, oa);
         if (t < P * P) {
           T ob[PO];
           sipg_rows2<PO, P, NN, OFF>(ox, vq, hl[q][0], hl[q][1], ob);
-          i3_st_pairs<PO>(RA + P * SA1 + dst, ob);
+          i3_st_pairs<PO>(RAA + P * SA1 + dst, ob);
         }
       }
     });
@@ -252,42 +287,45 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
   //   C = M_y A,  D = L_y [A with the y halos] + M_y B;
   // then 2 PO lines (r0, side): CZ = M_y (z halo face after M_x)
   constexpr int L2 = PO * P + 2 * PO;
-  constexpr int R2 = (L2 + TPP - 1) / TPP;
+  constexpr int R2 = (L2 + TPA - 1) / TPA;
   T* Cc = RB;
   T* Dd = RB + P * SC;
   T* CZ = RB + 2 * P * SC;
-  if (valid) {
+  T* CcA = RBA;  // the sweep's patch (WP: the warp's)
+  T* DdA = RBA + P * SC;
+  T* CZA = RBA + 2 * P * SC;
+  if (vA) {
     i3_with_type<BND>(ty[1], [&](auto tc) {
       const Ops& oy = ops.t[decltype(tc)::value];
 #pragma unroll
       for (int q = 0; q < R2; ++q) {
-        const int t = lane + q * TPP;
+        const int t = lA + q * TPA;
         if (t >= L2) continue;
         if (t < PO * P) {
           const int r0 = t % PO, a2 = t / PO;
           T va[P], vb[P], oc[PO], od[PO];
 #pragma unroll
           for (int a1 = 0; a1 < P; ++a1) {
-            va[a1] = RA[SA1 * a1 + t];
-            vb[a1] = RA[P * SA1 + SA1 * a1 + t];
+            va[a1] = RAA[SA1 * a1 + t];
+            vb[a1] = RAA[P * SA1 + SA1 * a1 + t];
           }
-          const T h0 = RA[2 * P * SA1 + t], h1 = RA[(2 * P + 1) * SA1 + t];
+          const T h0 = RAA[2 * P * SA1 + t], h1 = RAA[(2 * P + 1) * SA1 + t];
           mass_rows2<PO, P, NN, OFF, false>(oy, va, oc);
           sipg_rows2<PO, P, NN, OFF>(oy, va, h0, h1, od);
           mass_rows2<PO, P, NN, OFF, true>(oy, vb, od);
 #pragma unroll
           for (int r1 = 0; r1 < PO; ++r1) {
-            Cc[SC * a2 + PO * r1 + r0] = oc[r1];
-            Dd[SC * a2 + PO * r1 + r0] = od[r1];
+            CcA[SC * a2 + PO * r1 + r0] = oc[r1];
+            DdA[SC * a2 + PO * r1 + r0] = od[r1];
           }
         } else {
           const int h = t - PO * P, r0 = h % PO, side = h / PO;
           T vz[P], oc[PO];
 #pragma unroll
-          for (int a1 = 0; a1 < P; ++a1) vz[a1] = RA[(2 * P + 2 + side) * SA1 + PO * a1 + r0];
+          for (int a1 = 0; a1 < P; ++a1) vz[a1] = RAA[(2 * P + 2 + side) * SA1 + PO * a1 + r0];
           mass_rows2<PO, P, NN, OFF, false>(oy, vz, oc);
 #pragma unroll
-          for (int r1 = 0; r1 < PO; ++r1) CZ[side * CZS + PO * r1 + r0] = oc[r1];
+          for (int r1 = 0; r1 < PO; ++r1) CZA[side * CZS + PO * r1 + r0] = oc[r1];
         }
       }
     });
@@ -436,7 +474,7 @@ __global__ void __launch_bounds__(I3<NN, T, BND, TILE>::THREADS, I3<NN, T, BND, 
   T* dinv = reinterpret_cast<T*>(smem_raw);
   if constexpr (!BND) int3_dinv<NN, T>(ops.t[0], dinv);  // read after the first CTA barrier of the body
   const long long col = (long long)blockIdx.y * ndofs;
-  int3_body<NN, T, BND, C::PPC, true, C::PF>(ops, dinv, reinterpret_cast<T*>(smem_raw + C::PREFIX), (long long)blockIdx.x * C::PPC,
+  int3_body<NN, T, BND, C::PPC, true, C::PF, TILE>(ops, dinv, reinterpret_cast<T*>(smem_raw + C::PREFIX), (long long)blockIdx.x * C::PPC,
                                 colour, b + col, x + col, N, consistent, grid);
 }
 

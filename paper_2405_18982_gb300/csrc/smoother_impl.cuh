@@ -947,6 +947,7 @@ cudaError_t launch_patches(const sipg_handle* h, int level, int colour, const T*
           case 1: return launch_int3<NN, T, BND, 1>(h, level, colour, b, x, g, s);
           case 2: return launch_int3<NN, T, BND, 2>(h, level, colour, b, x, g, s);
           case 3: return launch_int3<NN, T, BND, 3>(h, level, colour, b, x, g, s);
+          case 4: return launch_int3<NN, T, BND, 4>(h, level, colour, b, x, g, s);
           default: break;
         }
       return launch_int3<NN, T, BND, 0>(h, level, colour, b, x, g, s);

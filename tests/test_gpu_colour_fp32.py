@@ -38,6 +38,7 @@ PATHS = {"pinned": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TIL
          "pinned_half_tile": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "1"},
          "pinned_prefetch": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "2"},
          "pinned_prefetch_3cta": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "3"},
+         "pinned_warp_sweeps": {"SIPG_AUTOTUNE": "0", "SIPG_FUSED_SMOOTHING": "0", "SIPG_TILE": "4"},
          "tuned": {}}
 VARIANTS = {"consistent": SIPG_SMOOTHER_CONSISTENT, "paper": SIPG_SMOOTHER_PAPER}
 TOL = 1e-4
