@@ -42,11 +42,12 @@
  * Tuning (read by sipg_create): SIPG_FUSED_SMOOTHING=0 in the environment
  * turns off the single cooperative launch per smoothing step on small levels
  * (the colours are then launched one by one; the results are the same);
- * SIPG_AUTOTUNE=0 skips the bind-time autotuning (sipg_tuning); SIPG_TILE=0..3
+ * SIPG_AUTOTUNE=0 skips the bind-time autotuning (sipg_tuning); SIPG_TILE=0..4
  * pins the interior tile of the 3D FP32 colour pass on every level, whatever
  * the autotuner measured: 0 the default patches per CTA, 1 half as many, 2 the
  * default tile with b and x on V_j loaded ahead of the sweeps that use them, 3
- * that tile at three CTAs per SM (more registers per thread).
+ * that tile at three CTAs per SM (more registers per thread), 4 tile 3 with
+ * the x and y sweeps on whole warps (each patch's lines on its own warps).
  */
 #ifndef SIPG_H
 #define SIPG_H
@@ -282,7 +283,7 @@ sipg_status sipg_dot(sipg_handle* h, const double* a, const double* b, double* o
  * for the V-cycle precision, every launch path of one smoothing step on the
  * level's scratch vectors and keeps the fastest; this reports the choice.
  * *path: -1 not tuned (default rules), 0 one fused launch per step, 1 colour
- * by colour.  *tile: interior tile of the 3D FP32 colour pass (0..3, as
+ * by colour.  *tile: interior tile of the 3D FP32 colour pass (0..4, as
  * SIPG_TILE above).  precision: SIPG_FP64 or SIPG_FP32.
  * EINVAL for a bad level or precision or null outputs. */
 sipg_status sipg_tuning(const sipg_handle* h, int level, int precision, int* path, int* tile);

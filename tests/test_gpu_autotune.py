@@ -20,7 +20,7 @@ def test_choices_valid(case):
     for lev in range(1, nl):
         path, tile = s.tuning(lev)
         assert path in (0, 1)
-        assert tile in (0, 1, 2, 3)
+        assert tile in (0, 1, 2, 3, 4)
         if not (dim == 3 and prec == SIPG_FP32):
             assert tile == 0
 

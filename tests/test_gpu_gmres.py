@@ -94,11 +94,14 @@ def test_gmres_restarts_and_warm_start(graphs):
 
 @pytest.mark.parametrize("prec,left", [(SIPG_FP64, False), (SIPG_FP32, False), (SIPG_FP64, True)],
                          ids=["fp64-right", "mixed-right", "fp64-left"])
-def test_device_cycles_equal_host_steps(prec, left):
+def test_device_cycles_equal_host_steps(prec, left, monkeypatch):
     # the same GMRES driven step by step from the host and as one graph
     # launch per restart cycle: same steps, histories and solutions up to
     # rounding (the rotations run on the host in one and on the device in
-    # the other); short restarts and a step limit that ends inside a cycle
+    # the other); short restarts and a step limit that ends inside a cycle.
+    # Both handles take the default launch paths (no autotuning), so that
+    # their FP32 V-cycles run the same kernels and round alike.
+    monkeypatch.setenv("SIPG_AUTOTUNE", "0")
     dim, k, l2, nl = 3, 3, 4, 3
     N = 1 << l2
     b = rhs_from_nodal(dim, k, N, inputs.normal(760, (N * (k + 1)) ** 3))
