@@ -1131,9 +1131,12 @@ sipg_status sipg_smooth_colour(sipg_handle* h, int level, int prec, int colour, 
                       ? launch_smooth_colour<double>(h, level, colour, (const double*)b, (double*)x, S(stream))
                       : launch_smooth_colour<float>(h, level, colour, (const float*)b, (float*)x, S(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "smoother");
-  const bool full = h->prm.smoother == SIPG_SMOOTHER_FULL ||
-                    (h->prm.smoother == SIPG_SMOOTHER_CLAMPED && !(h->prm.dim == 3 && prec == SIPG_FP32));
-  h->launches += full ? 2 : colour_kernels(h->prm.dim, h->lv[level].N, colour);
+  const bool fp32_3d = h->prm.dim == 3 && prec == SIPG_FP32;
+  const bool full = h->prm.smoother == SIPG_SMOOTHER_FULL || (h->prm.smoother == SIPG_SMOOTHER_CLAMPED && !fp32_3d);
+  // full kernel: the residual apply, then the patch kernel (3D FP32: one per
+  // patch set, interior and boundary)
+  h->launches += full ? (fp32_3d ? 1 + colour_kernels(3, h->lv[level].N, colour) : 2)
+                      : colour_kernels(h->prm.dim, h->lv[level].N, colour);
   return SIPG_OK;
 }
 

@@ -17,13 +17,16 @@
 // residuals, so one global residual per colour gives the multiplicative
 // result.
 //
-// Patch kernel: a patch's P^d residual values (P = 2n) are staged in shared
-// memory in patch-lexicographic order (direction 0 fastest); each thread owns
+// Patch kernel (FP64, and 2D): a patch's P^d residual values (P = 2n) are
+// staged in shared memory in patch-lexicographic order (direction 0 fastest); each thread owns
 // one line per direction and applies S^T along directions 0..d-1, the
 // eigenvalue scaling, then S along each direction, and finally adds its
 // direction-0 line to x.  The 1D eigenvectors are read from the level
 // constants in global memory (a few KB, L1-resident).
 #include "sipg_internal.cuh"
+
+template <int NN>
+cudaError_t full3_colour_n(const sipg_handle* h, int level, int colour, const float* r, float* x, cudaStream_t s);
 
 namespace {
 
@@ -181,6 +184,24 @@ cudaError_t launch_full_colour(const sipg_handle* h, int level, int colour, cons
   cudaError_t e = launch_apply<T>(h, level, APPLY_RESIDUAL, b, x, r, s);
   if (e != cudaSuccess) return e;
   *launches = 1;
+  if constexpr (sizeof(T) == 4) {
+    // 3D FP32 full kernel: the register-direct all-rows patch kernels
+    if (h->prm.dim == 3 && h->prm.smoother == SIPG_SMOOTHER_FULL) {
+      const float* rf = reinterpret_cast<const float*>(r);
+      float* xf = reinterpret_cast<float*>(x);
+      switch (h->n) {
+        case 2: e = full3_colour_n<2>(h, level, colour, rf, xf, s); break;
+        case 3: e = full3_colour_n<3>(h, level, colour, rf, xf, s); break;
+        case 4: e = full3_colour_n<4>(h, level, colour, rf, xf, s); break;
+        case 5: e = full3_colour_n<5>(h, level, colour, rf, xf, s); break;
+        case 6: e = full3_colour_n<6>(h, level, colour, rf, xf, s); break;
+        case 7: e = full3_colour_n<7>(h, level, colour, rf, xf, s); break;
+        default: e = full3_colour_n<8>(h, level, colour, rf, xf, s); break;
+      }
+      if (e == cudaSuccess) *launches = 1 + colour_kernels(3, h->lv[level].N, colour);
+      return e;
+    }
+  }
   e = h->prm.dim == 2 ? full_dim<2, T>(h, level, colour, r, x, s) : full_dim<3, T>(h, level, colour, r, x, s);
   if (e == cudaSuccess) *launches = 2;
   return e;

@@ -5,10 +5,13 @@
 
 SIPG_SMOOTH_INST(3, float, 2)
 SIPG_CLAMPED_INST(2)
+SIPG_FULL3_INST(2)
 SIPG_SMOOTH_INST(3, float, 3)
 SIPG_CLAMPED_INST(3)
+SIPG_FULL3_INST(3)
 SIPG_SMOOTH_INST(3, float, 4)
 SIPG_CLAMPED_INST(4)
+SIPG_FULL3_INST(4)
 
 cudaError_t launch_barrier_selftest(const sipg_handle* h, int extra, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};

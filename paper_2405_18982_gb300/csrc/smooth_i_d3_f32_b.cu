@@ -5,5 +5,7 @@
 
 SIPG_SMOOTH_INST(3, float, 5)
 SIPG_CLAMPED_INST(5)
+SIPG_FULL3_INST(5)
 SIPG_SMOOTH_INST(3, float, 6)
 SIPG_CLAMPED_INST(6)
+SIPG_FULL3_INST(6)

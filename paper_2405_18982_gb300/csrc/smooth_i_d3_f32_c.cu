@@ -5,5 +5,7 @@
 
 SIPG_SMOOTH_INST(3, float, 7)
 SIPG_CLAMPED_INST(7)
+SIPG_FULL3_INST(7)
 SIPG_SMOOTH_INST(3, float, 8)
 SIPG_CLAMPED_INST(8)
+SIPG_FULL3_INST(8)

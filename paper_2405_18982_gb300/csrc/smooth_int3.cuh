@@ -131,7 +131,14 @@ __device__ __forceinline__ void int3_dinv(const Ops1D<2 * NN - 2, 2 * NN, T>& o0
 // read-only (non-coherent) path, valid when no other CTA writes what this
 // launch reads (one colour per launch); the fused step, whose later colours
 // read what other CTAs wrote, uses coherent loads.
-template <int NN, typename T, bool BND, int PPC, bool NC, bool PF = false, int TILE = 0>
+// FULL (with BND): the full kernel's local solve (Sec. 3.1, Table 1) on all
+// P = 2n patch nodes per direction: the patch residual is read from the
+// global residual vector passed as b (no residual sweeps), then the same
+// transforms with the whole-patch eigenpairs in ops; FINT: the patches are
+// the colour's interior ones (interior decode) in this all-rows layout,
+// otherwise the shell of patches touching the domain boundary.
+template <int NN, typename T, bool BND, int PPC, bool NC, bool PF = false, int TILE = 0, bool FULL = false,
+          bool FINT = false>
 __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 * NN, T, I3<NN, T, BND>::NT>& ops,
                                           const T* dinv, T* buf, long long pbase, int colour,
                                           const T* __restrict__ b, T* x, int N, int consistent,
@@ -146,11 +153,12 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
   T* RA = buf + (size_t)(pl < PPC ? pl : 0) * C::PS;
   T* RB = RA + C::RA;
 
-  const long long npatch = BND ? grid.n_bnd : grid.n_int;
+  static_assert(!FULL || BND, "the full kernel's pass uses the all-rows layout");
+  const long long npatch = (BND && !FINT) ? grid.n_bnd : grid.n_int;
   const long long pidx = pbase + pl;
   const bool valid = pl < PPC && pidx < npatch;
   int v[3], ty[3] = {0, 0, 0};
-  if (BND) {
+  if (BND && !FINT) {
     int m[3] = {0, 0, 0};
     patch_index<3, true>(grid, valid ? pidx : 0, m);
 #pragma unroll
@@ -215,7 +223,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
   // slot 0/1 = y faces below/above (j = a2), 2/3 = z faces (j = a1), M_x only
   constexpr int L1 = P * P + 4 * P;
   constexpr int R1 = (L1 + TPA - 1) / TPA;
-  if (vA) {
+  if (!FULL && vA) {
     T vin[R1][P], hl[R1][2];
 #pragma unroll
     for (int q = 0; q < R1; ++q) {
@@ -280,7 +288,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       for (int r2 = 0; r2 < PO; ++r2) bvp[r2] = __ldg(gbp + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN);
     }
   }
-  __syncthreads();
+  if constexpr (!FULL) __syncthreads();
 
   // ------------------------------------------------------------------ y sweep
   // lines t < PO P: (r0, a2) = (t % PO, t / PO):
@@ -294,7 +302,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
   T* CcA = RBA;  // the sweep's patch (WP: the warp's)
   T* DdA = RBA + P * SC;
   T* CZA = RBA + 2 * P * SC;
-  if (vA) {
+  if (!FULL && vA) {
     i3_with_type<BND>(ty[1], [&](auto tc) {
       const Ops& oy = ops.t[decltype(tc)::value];
 #pragma unroll
@@ -330,7 +338,7 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
       }
     });
   }
-  __syncthreads();
+  if constexpr (!FULL) __syncthreads();
 
   // ------------------------------------------------ z sweep, residual, S_z^T
   // line (r0, r1) = (lane % PO, lane / PO); patch node (r0, r1, r2) + OFF
@@ -361,17 +369,25 @@ __device__ __forceinline__ void int3_body(const SmoothOps<I3<NN, T, BND>::PO, 2 
         else
           bv[r2] = in ? __ldg(gb + ((r2 + OFF) / NN) * cs2 + ((r2 + OFF) % NN) * NN * NN) : T(0);
       }
+      if constexpr (FULL) {
 #pragma unroll
-      for (int a2 = 0; a2 < P; ++a2) {
-        vc[a2] = Cc[SC * a2 + lane];
-        vd[a2] = Dd[SC * a2 + lane];
-      }
-      sipg_rows2<PO, P, NN, OFF>(oz, vc, CZ[lane], CZ[CZS + lane], o);
-      mass_rows2<PO, P, NN, OFF, true>(oz, vd, o);
+        for (int r2 = 0; r2 < PO; ++r2) {
+          const bool in = inxy && r2 >= zlo && r2 <= zhi;
+          o[r2] = in ? bv[r2] : T(0);  // the global residual on the patch
+        }
+      } else {
 #pragma unroll
-      for (int r2 = 0; r2 < PO; ++r2) {
-        const bool in = inxy && r2 >= zlo && r2 <= zhi;
-        o[r2] = in ? bv[r2] - o[r2] : T(0);
+        for (int a2 = 0; a2 < P; ++a2) {
+          vc[a2] = Cc[SC * a2 + lane];
+          vd[a2] = Dd[SC * a2 + lane];
+        }
+        sipg_rows2<PO, P, NN, OFF>(oz, vc, CZ[lane], CZ[CZS + lane], o);
+        mass_rows2<PO, P, NN, OFF, true>(oz, vd, o);
+#pragma unroll
+        for (int r2 = 0; r2 < PO; ++r2) {
+          const bool in = inxy && r2 >= zlo && r2 <= zhi;
+          o[r2] = in ? bv[r2] - o[r2] : T(0);
+        }
       }
       st_rows2<PO>(oz.S2, o, t1);
 #pragma unroll
@@ -636,6 +652,63 @@ cudaError_t launch_int3_clamped(const sipg_handle* h, int level, int colour, con
     for (int t = 0; t < CB::NT; ++t) make_ops_clamped<NN, T>(h->hcst<T>(level), t, ops.t[t]);
     dim3 grid((unsigned)((g.n_bnd + CB::PPC - 1) / CB::PPC), h->prm.nrhs);
     smooth_int3_kernel<NN, T, true, 0><<<grid, CB::THREADS, CB::SMEM, sb>>>(ops, colour, b, x, N, 0, nd, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (fork) {
+    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ full
+// The full kernel's patch solves (Sec. 3.1, Table 1) in the register-direct
+// all-rows layout: after the whole-level residual r = b - A x of the colour,
+// every patch of the colour adds A_j^{-1} R_j r, A_j^{-1} = (S (x) S (x) S)
+// Lambda^{-1} (...)^T with the whole-patch eigenpairs of the patch's 1D
+// types.  Interior and boundary patches run as two launches (two streams);
+// same-colour patches write disjoint nodes and read only r.
+template <int NN, bool FINT>
+__global__ void __launch_bounds__(I3<NN, float, true>::THREADS, I3<NN, float, true>::MINB)
+    smooth_full3_kernel(const __grid_constant__ SmoothOps<2 * NN, 2 * NN, float, 4> ops, int colour,
+                        const float* __restrict__ r, float* x, int N, long long ndofs, PatchGrid grid) {
+  using C = I3<NN, float, true>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long col = (long long)blockIdx.y * ndofs;
+  int3_body<NN, float, true, C::PPC, true, false, 0, true, FINT>(ops, nullptr,
+                                                               reinterpret_cast<float*>(smem_raw + C::PREFIX),
+                                                               (long long)blockIdx.x * C::PPC, colour, r + col,
+                                                               x + col, N, 0, grid);
+}
+
+template <int NN>
+cudaError_t launch_full3(const sipg_handle* h, int level, int colour, const float* r, float* x, cudaStream_t s) {
+  using C = I3<NN, float, true>;
+  const PatchGrid g = make_grid(3, h->lv[level].N, colour);
+  if (g.n_int + g.n_bnd <= 0) return cudaSuccess;
+  const int N = h->lv[level].N;
+  const long long nd = (long long)h->lv[level].ndofs;
+  SmoothOps<2 * NN, 2 * NN, float, 4> ops;
+  for (int t = 0; t < 4; ++t) make_ops_clamped<NN, float>(h->hcst<float>(level), t, ops.t[t]);
+  cudaError_t e;
+  const bool fork = g.n_int > 0 && g.n_bnd > 0 && h->side;
+  cudaStream_t sb = fork ? h->side : s;
+  if (fork) {
+    if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+  }
+  if (g.n_int > 0) {
+    e = smem_opt_in(reinterpret_cast<const void*>(smooth_full3_kernel<NN, true>), (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.n_int + C::PPC - 1) / C::PPC), h->prm.nrhs);
+    smooth_full3_kernel<NN, true><<<grid, C::THREADS, C::SMEM, s>>>(ops, colour, r, x, N, nd, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (g.n_bnd > 0) {
+    e = smem_opt_in(reinterpret_cast<const void*>(smooth_full3_kernel<NN, false>), (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((g.n_bnd + C::PPC - 1) / C::PPC), h->prm.nrhs);
+    smooth_full3_kernel<NN, false><<<grid, C::THREADS, C::SMEM, sb>>>(ops, colour, r, x, N, nd, g);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (fork) {

@@ -1149,6 +1149,15 @@ cudaError_t clamped_colour3_n(const sipg_handle* h, int level, int colour, const
 #define SIPG_CLAMPED_INST(NN)                                                                                 \
   template cudaError_t clamped_colour3_n<NN>(const sipg_handle*, int, int, const float*, float*, cudaStream_t);
 
+// The full kernel's patch solves of one colour (3D FP32) from the level's
+// residual r (the caller computes it).
+template <int NN>
+cudaError_t full3_colour_n(const sipg_handle* h, int level, int colour, const float* r, float* x, cudaStream_t s) {
+  return launch_full3<NN>(h, level, colour, r, x, s);
+}
+#define SIPG_FULL3_INST(NN)                                                                                   \
+  template cudaError_t full3_colour_n<NN>(const sipg_handle*, int, int, const float*, float*, cudaStream_t);
+
 #define SIPG_SMOOTH_INST(DIM, T, NN)                                                                         \
   template cudaError_t smooth_colour_n<DIM, T, NN>(const sipg_handle*, int, int, const T*, T*, cudaStream_t); \
   template cudaError_t smooth_step_n<DIM, T, NN>(const sipg_handle*, int, int, const T*, T*, cudaStream_t);

@@ -24,11 +24,11 @@ def local_nodes(dim, n):
     return np.stack([(idx // n ** e) % n for e in range(dim)], axis=1)
 
 
-def patch_cells_and_mask(dim, k, N, v):
+def patch_cells_and_mask(dim, k, N, v, full=False):
     """Flat numbers of the 2^d cells of the patch at interior vertex v
     (ascending) and the boolean mask of the Dirichlet space V_j over their
     DoFs (patch-boundary nodes removed, except at ends on the domain
-    boundary)."""
+    boundary; full: every DoF of the patch cells, the full kernel's space)."""
     n = k + 1
     loc = local_nodes(dim, n)
     cells, mask = [], []
@@ -37,9 +37,10 @@ def patch_cells_and_mask(dim, k, N, v):
         cells.append(cell_id(dim, N, [v[e] - 1 + o[e] for e in range(dim)]))
         a = np.array(o)[None, :] * n + loc
         ok = np.ones(n ** dim, bool)
-        for e in range(dim):
-            ok &= (a[:, e] != 0) | (v[e] == 1)
-            ok &= (a[:, e] != 2 * n - 1) | (v[e] == N - 1)
+        if not full:
+            for e in range(dim):
+                ok &= (a[:, e] != 0) | (v[e] == 1)
+                ok &= (a[:, e] != 2 * n - 1) | (v[e] == N - 1)
         mask.append(ok)
     return cells, np.concatenate(mask)
 
@@ -63,9 +64,9 @@ def sample_vertices(dim, N, colour, seed, count):
     return sorted(out)
 
 
-def colour_touch_mask(dim, k, N, colour):
+def colour_touch_mask(dim, k, N, colour, full=False):
     """Boolean mask over all DoFs: True where some patch of `colour` has the
-    DoF in its Dirichlet space V_j.  Along direction e a DoF of cell c_e, node
+    DoF in its Dirichlet space V_j (full: in one of its cells).  Along direction e a DoF of cell c_e, node
     i_e lies in the patch with vertex v_e = c_e (it is in the upper patch cell)
     or v_e = c_e + 1 (lower patch cell), whichever has the colour's parity."""
     n = k + 1
@@ -81,7 +82,7 @@ def colour_touch_mask(dim, k, N, colour):
         a = np.where(upper[:, None], n + loc[None, :, e], loc[None, :, e])
         inside = (v >= 1) & (v <= N - 1)
         good = ((a != 0) | (v[:, None] == 1)) & ((a != 2 * n - 1) | (v[:, None] == N - 1))
-        ok &= inside[:, None] & good
+        ok &= inside[:, None] & (True if full else good)
     return ok.ravel()
 
 
@@ -91,6 +92,7 @@ class PatchOracle:
     boundary)."""
 
     def __init__(self, dim, k, N, variant="consistent", kappa=1.0, eta=1.0):
+        # variant "full": the full kernel (every patch DoF, the global residual)
         self.dim, self.k, self.N, self.variant = dim, k, N, variant
         self.blocks = element_blocks(dim, k, N, kappa, eta)
         self.no_last = element_blocks(dim, k, N, kappa, eta, part="no_last") if variant == "paper" else None
@@ -112,14 +114,14 @@ class PatchOracle:
 
     def update(self, v, b, x0):
         """(global DoF indices of V_j, A_j^{-1} r_j) for the patch at vertex v,
-        r_j the local residual at x0 (consistent: R_j (b - A x0); paper:
-        R_j b - Abar_j Rbar_j x0, Sec. 3.1)."""
+        r_j the local residual at x0 (consistent and full: R_j (b - A x0);
+        paper: R_j b - Abar_j Rbar_j x0, Sec. 3.1)."""
         n = self.k + 1
         nl = n ** self.dim
-        cells, mask = patch_cells_and_mask(self.dim, self.k, self.N, v)
+        cells, mask = patch_cells_and_mask(self.dim, self.k, self.N, v, full=self.variant == "full")
         dofs = np.concatenate([np.arange(nl) + c * nl for c in cells])
         chol, Abar = self._factors(v, cells, mask)
-        if self.variant == "consistent":
+        if self.variant in ("consistent", "full"):
             Ax = block_apply(self.dim, self.k, self.N, self.blocks, x0, cells).ravel()[mask]
         else:
             Ax = Abar @ x0[dofs]

@@ -48,6 +48,37 @@ def test_full_colour_pass_fp32(case, kernel):
         assert np.abs(host(xd) - x).max() <= 1e-4 * np.abs(x - x0).max(), f"colour {c}"
 
 
+@pytest.mark.parametrize("case", [(2, 5), (3, 5), (4, 4), (5, 4)], ids=lambda c: f"k{c[0]}N{1 << c[1]}")
+def test_full_colour_pass_fp32_sampled(case):
+    # the full kernel's 3D FP32 pass (register-direct all-rows kernels, one
+    # launch for the interior and one for the boundary patches) on meshes
+    # where a colour spans many CTAs: sampled patches (first and last of each
+    # launch, every boundary type, random ones) against the oracle's dense
+    # solve with the global residual, every DoF outside the colour's patch
+    # cells bit-unchanged
+    import torch
+    from patch_sampling import PatchOracle, colour_touch_mask, sample_vertices
+    k, l2 = case
+    N = 1 << l2
+    s = make(3, k, l2, l2, prec=SIPG_FP32, smoother=SIPG_SMOOTHER_FULL)
+    nd = s.ndofs(l2 - 1)
+    b = inputs.normal(810 + k, nd).astype(np.float32).astype(np.float64)
+    x0 = inputs.normal(820 + k, nd).astype(np.float32).astype(np.float64)
+    bd = dev(b, torch.float32).view(1, -1)
+    po = PatchOracle(3, k, N, "full")
+    for c in range(8):
+        xd = dev(x0, torch.float32).view(1, -1)
+        s.smooth_colour(l2 - 1, c, bd, xd)
+        x1 = host(xd).ravel()
+        touch = colour_touch_mask(3, k, N, c, full=True)
+        assert np.array_equal(x1[~touch], x0[~touch]), f"colour {c} wrote outside its patch cells"
+        du = x1 - x0
+        for v in sample_vertices(3, N, c, 830 + c, 10):
+            idx, u = po.update(v, b, x0)
+            err = np.abs(du[idx] - u).max() / np.abs(u).max()
+            assert err < 1e-4, (c, v, err)
+
+
 @pytest.mark.parametrize("kernel", list(KERNELS), ids=list(KERNELS.values()))
 @pytest.mark.parametrize("prec", [SIPG_FP64, SIPG_FP32], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES[1:4], ids=IDS[1:4])

@@ -1,7 +1,7 @@
 """The sampled-patch helpers used by the large-mesh GPU parity tests agree
 with the oracle's own colour pass (dense assembled patch solves) on meshes
 small enough for it: every patch of a colour, and the set of DoFs a colour
-may touch."""
+may touch, for the Dirichlet kernel (both residuals) and the full kernel."""
 import numpy as np
 import pytest
 
@@ -10,7 +10,7 @@ from paper_2405_18982_gb300 import inputs
 from patch_sampling import PatchOracle, colour_touch_mask, sample_vertices
 
 
-@pytest.mark.parametrize("variant", ["consistent", "paper"])
+@pytest.mark.parametrize("variant", ["consistent", "paper", "full"])
 @pytest.mark.parametrize("case", [(2, 2, 8), (2, 3, 4), (3, 2, 4), (3, 1, 2)], ids=lambda c: f"d{c[0]}k{c[1]}N{c[2]}")
 def test_patch_oracle_equals_colour_pass(case, variant):
     dim, k, N = case
@@ -20,7 +20,7 @@ def test_patch_oracle_equals_colour_pass(case, variant):
     po = PatchOracle(dim, k, N, variant)
     for c in range(2 ** dim):
         x1 = smooth(lev, x0, b, colours=[c])
-        mask = colour_touch_mask(dim, k, N, c)
+        mask = colour_touch_mask(dim, k, N, c, full=variant == "full")
         # outside the colour's spaces nothing changes; inside, something may
         assert np.array_equal(x1[~mask], x0[~mask])
         union = np.zeros(lev.ndof, bool)
