@@ -48,6 +48,9 @@
  * default tile with b and x on V_j loaded ahead of the sweeps that use them, 3
  * that tile at three CTAs per SM (more registers per thread), 4 tile 3 with
  * the x and y sweeps on whole warps (each patch's lines on its own warps).
+ * SIPG_BOUNDARY_FIRST=0 launches the interior-patch kernel of a colour pass
+ * before the boundary-patch kernel (default: boundary patches first, at the
+ * greatest stream priority; the results are the same).
  */
 #ifndef SIPG_H
 #define SIPG_H

@@ -912,6 +912,7 @@ sipg_status sipg_create(const sipg_params* p, sipg_handle** out) {
   // colour; SIPG_AUTOTUNE=0 skips the bind-time timing of the launch paths
   if (const char* env = getenv("SIPG_FUSED_SMOOTHING")) h->fuse_small_levels = atoi(env) != 0;
   if (const char* env = getenv("SIPG_AUTOTUNE")) h->autotune = atoi(env) != 0;
+  if (const char* env = getenv("SIPG_BOUNDARY_FIRST")) h->bnd_first = atoi(env) != 0;
   if (const char* env = getenv("SIPG_TILE")) {
     const int t = atoi(env);
     h->force_tile = (t >= 0 && t <= 4) ? t : 0;

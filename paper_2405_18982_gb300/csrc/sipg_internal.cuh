@@ -152,6 +152,10 @@ struct sipg_handle {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int prio_hi = 0;  // greatest launch priority of the device: the interior kernel of a colour pass
+  // colour passes: the boundary-patch kernel is launched first and at
+  // prio_hi, the interior one fills the SMs behind it (SIPG_BOUNDARY_FIRST=0:
+  // the other way round)
+  bool bnd_first = true;
   // host copies of the device-computed level constants (read back once at
   // bind time; kernels receive the small 1D operators as launch parameters)
   std::vector<LevelConst<double>> hc64;

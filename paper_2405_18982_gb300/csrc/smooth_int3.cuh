@@ -513,7 +513,7 @@ cudaError_t launch_int3(const sipg_handle* h, int level, int colour, const T* b,
   la[0].id = cudaLaunchAttributePriority;
   la[0].val.priority = h->prio_hi;
   cfg.attrs = la;
-  cfg.numAttrs = BND ? 0 : 1;  // interior patches first (see the colour-pass dispatch)
+  cfg.numAttrs = (BND == h->bnd_first) ? 1 : 0;  // the patch set launched first (see the colour-pass dispatch)
   return cudaLaunchKernelEx(&cfg, smooth_int3_kernel<NN, T, BND, TILE>, ops, colour, b, x, h->lv[level].N,
                             h->prm.smoother == SIPG_SMOOTHER_CONSISTENT ? 1 : 0, (long long)h->lv[level].ndofs, g);
 }
