@@ -142,7 +142,9 @@ __global__ void __launch_bounds__(RB) finalize_kernel(int mode, KrylovScalars* s
   }
 }
 
-// z = double(zsrc) (if zsrc differs), partial <r, z> and <z, q>.
+// partial <r, z> and <z, q> with z = double(zsrc); z is also stored when
+// the pointer is given and differs from zsrc (an FP32 V-cycle output is read
+// again by p_update_kernel instead).
 template <typename TZ>
 __global__ void __launch_bounds__(RB) precond_post_kernel(const TZ* zsrc, double* z, const double* r,
                                                           const double* q, long long n, double* partials,
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(RB) precond_post_kernel(const TZ* zsrc, double
   const long long stride = (long long)gridDim.x * RB;
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
     double zi = (double)zsrc[col + i];
-    if ((const void*)zsrc != (const void*)z) z[col + i] = zi;
+    if (z && (const void*)zsrc != (const void*)z) z[col + i] = zi;
     v[0] = fma(r[col + i], zi, v[0]);
     if (want_zq) v[1] = fma(zi, q[col + i], v[1]);
   }
@@ -165,13 +167,17 @@ __global__ void __launch_bounds__(RB) precond_post_kernel(const TZ* zsrc, double
   }
 }
 
-__global__ void __launch_bounds__(RB) p_update_kernel(int first, const double* z, double* p,
+// p = z + beta p (p = z first), z = double(z_src)
+template <typename TZ>
+__global__ void __launch_bounds__(RB) p_update_kernel(int first, const TZ* z, double* p,
                                                       const KrylovScalars* sc, long long n) {
   const long long col = (long long)blockIdx.y * n;
   const double beta = first ? 0.0 : sc[blockIdx.y].beta;
   const long long stride = (long long)gridDim.x * RB;
-  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride)
-    p[col + i] = first ? z[col + i] : fma(beta, p[col + i], z[col + i]);
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+    const double zi = (double)z[col + i];
+    p[col + i] = first ? zi : fma(beta, p[col + i], zi);
+  }
 }
 
 // x += alpha p, r -= alpha q, partial ||r||^2, optional V-cycle input bL = r.
@@ -492,15 +498,20 @@ cudaError_t krylov_init_norms(sipg_handle* h, const double* b, const double* r, 
 cudaError_t krylov_after_precond(sipg_handle* h, int first, const double* r, const void* zsrc,
                                  int zsrc_is_float, cudaStream_t s) {
   dim3 grid(h->n_partials, h->prm.nrhs);
+  // an FP32 V-cycle output stays in its buffer: the dots and the direction
+  // update convert it on the fly (no FP64 copy of z is written)
   if (zsrc_is_float)
-    precond_post_kernel<float><<<grid, RB, 0, s>>>((const float*)zsrc, h->kz(), r, h->kq(), fine_n(h),
+    precond_post_kernel<float><<<grid, RB, 0, s>>>((const float*)zsrc, nullptr, r, h->kq(), fine_n(h),
                                                    h->partials(), first ? 0 : 1);
   else
     precond_post_kernel<double><<<grid, RB, 0, s>>>((const double*)zsrc, h->kz(), r, h->kq(), fine_n(h),
                                                     h->partials(), first ? 0 : 1);
   finalize_kernel<<<h->prm.nrhs, RB, 0, s>>>(first ? FIN_RHO_FIRST : FIN_RHO_NEXT, h->scalars(),
                                              h->partials(), h->n_partials, h->rtol2, nullptr);
-  p_update_kernel<<<grid, RB, 0, s>>>(first, h->kz(), h->kp(), h->scalars(), fine_n(h));
+  if (zsrc_is_float)
+    p_update_kernel<float><<<grid, RB, 0, s>>>(first, (const float*)zsrc, h->kp(), h->scalars(), fine_n(h));
+  else
+    p_update_kernel<double><<<grid, RB, 0, s>>>(first, h->kz(), h->kp(), h->scalars(), fine_n(h));
   h->launches += 3;
   return cudaGetLastError();
 }
