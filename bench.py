@@ -762,12 +762,21 @@ def run_sweep(args):
     """--mode sweep: MDoF/s of the finest-level apply, one smoothing step, one
     V-cycle (FP32) and one mixed solve to 1e-10, over 3D k = 2..7 with
     N = 16, 32, 64 and 2D k = 2..7 with N = 512, 1024, 2048 (coarsest level 2
-    cells per direction; f ~ N(0,1), seed 3).  One JSON line per configuration."""
+    cells per direction; f ~ N(0,1), seed 3), with the roofline fraction of
+    the apply and the smoothing step (max(flop time, byte time) at the peaks
+    over the measured time, the counts of apply_counts and smoother_counts).
+    One JSON line per configuration."""
     import torch
     import paper_2405_18982_gb300 as pkg
     from paper_2405_18982_gb300 import SIPG, SIPG_FP32, Params, inputs
     pkg.load(pkg.build())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hbm, _ = measured_peaks()
+    peak32 = fp32_peak_tflops()
+
+    def frac(t, flops, nbytes):
+        floor = max(flops / (peak32 * 1e12), nbytes / (hbm * 1e9))
+        return round(floor / t, 4), ("alu" if flops / (peak32 * 1e12) >= nbytes / (hbm * 1e9) else "hbm")
 
     def timed(fn, reps):
         fn()
@@ -804,9 +813,19 @@ def run_sweep(args):
 
         info = solve()
         t_solve = timed(solve, 2)
+        N = 1 << l2
+        fa, ba = apply_counts(dim, k, N, 4)
+        fs, bs = 0, 0
+        for c in range(2 ** dim):
+            _, f_c, b_c, _ = smoother_counts(dim, k, N, c, 4)
+            fs, bs = fs + f_c, bs + b_c
+        fr_a, bd_a = frac(t_apply, fa, ba)
+        fr_s, bd_s = frac(t_smooth, fs, bs)
         print(json.dumps({"mode": "sweep", "dim": dim, "degree": k, "cells_per_dir": 1 << l2, "dofs": n,
                           "apply_fp32_mdofs": round(n / t_apply / 1e6, 1),
+                          "apply_roofline_frac": fr_a, "apply_bound": bd_a,
                           "smooth_step_fp32_mdofs": round(n / t_smooth / 1e6, 1),
+                          "smooth_step_roofline_frac": fr_s, "smooth_step_bound": bd_s,
                           "vcycle_fp32_mdofs": round(n / t_vc / 1e6, 1),
                           "solve_mixed_ms": round(t_solve * 1e3, 2), "iterations": info.iterations,
                           "solve_mdofs_per_vcycle": round(n * info.iterations / t_solve / 1e6, 1)}), flush=True)
