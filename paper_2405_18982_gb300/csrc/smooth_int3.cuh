@@ -526,6 +526,24 @@ bool use_int3(const PatchGrid& g, const void* b, const void* x) {
          (reinterpret_cast<uintptr_t>(x) % 16) == 0;
 }
 
+// A launch with the device's greatest stream priority when `prio` (the
+// patch set of a colour pass that goes first, see the colour-pass dispatch).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t s, bool prio,
+                        int prio_value, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute la[1];
+  la[0].id = cudaLaunchAttributePriority;
+  la[0].val.priority = prio_value;
+  cfg.attrs = la;
+  cfg.numAttrs = prio ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------- clamped
 // The clamped kernel (Sec. 3.1): V_j = patch functions with v = d_n v = 0 on
 // the patch boundary inside the domain.  Every face term of the patch
@@ -636,24 +654,30 @@ cudaError_t launch_int3_clamped(const sipg_handle* h, int level, int colour, con
     if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
   }
-  if (g.n_int > 0) {
-    e = smem_opt_in(reinterpret_cast<const void*>(smooth_int3_kernel<NN, T, false, 0>), (int)CI::SMEM);
-    if (e != cudaSuccess) return e;
+  // the boundary patches first at the greatest priority (as for the
+  // Dirichlet kernel), unless the handle says otherwise
+  auto run_int = [&]() -> cudaError_t {
+    if (g.n_int <= 0) return cudaSuccess;
+    cudaError_t ee = smem_opt_in(reinterpret_cast<const void*>(smooth_int3_kernel<NN, T, false, 0>), (int)CI::SMEM);
+    if (ee != cudaSuccess) return ee;
     SmoothOps<CI::PO, CI::P, T, 1> ops;
     make_ops_clamped_interior<NN, T>(h->hcst<T>(level), ops.t[0]);
     dim3 grid((unsigned)((g.n_int + CI::PPC - 1) / CI::PPC), h->prm.nrhs);
-    smooth_int3_kernel<NN, T, false, 0><<<grid, CI::THREADS, CI::SMEM, s>>>(ops, colour, b, x, N, 0, nd, g);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (g.n_bnd > 0) {
-    e = smem_opt_in(reinterpret_cast<const void*>(smooth_int3_kernel<NN, T, true, 0>), (int)CB::SMEM);
-    if (e != cudaSuccess) return e;
+    return launch_prio(smooth_int3_kernel<NN, T, false, 0>, grid, CI::THREADS, CI::SMEM, s, !h->bnd_first,
+                       h->prio_hi, ops, colour, b, x, N, 0, nd, g);
+  };
+  auto run_bnd = [&]() -> cudaError_t {
+    if (g.n_bnd <= 0) return cudaSuccess;
+    cudaError_t ee = smem_opt_in(reinterpret_cast<const void*>(smooth_int3_kernel<NN, T, true, 0>), (int)CB::SMEM);
+    if (ee != cudaSuccess) return ee;
     SmoothOps<CB::PO, CB::P, T, CB::NT> ops;
     for (int t = 0; t < CB::NT; ++t) make_ops_clamped<NN, T>(h->hcst<T>(level), t, ops.t[t]);
     dim3 grid((unsigned)((g.n_bnd + CB::PPC - 1) / CB::PPC), h->prm.nrhs);
-    smooth_int3_kernel<NN, T, true, 0><<<grid, CB::THREADS, CB::SMEM, sb>>>(ops, colour, b, x, N, 0, nd, g);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+    return launch_prio(smooth_int3_kernel<NN, T, true, 0>, grid, CB::THREADS, CB::SMEM, sb, h->bnd_first,
+                       h->prio_hi, ops, colour, b, x, N, 0, nd, g);
+  };
+  if ((e = h->bnd_first ? run_bnd() : run_int()) != cudaSuccess) return e;
+  if ((e = h->bnd_first ? run_int() : run_bnd()) != cudaSuccess) return e;
   if (fork) {
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;
@@ -697,20 +721,24 @@ cudaError_t launch_full3(const sipg_handle* h, int level, int colour, const floa
     if ((e = cudaEventRecord(h->ev_fork, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
   }
-  if (g.n_int > 0) {
-    e = smem_opt_in(reinterpret_cast<const void*>(smooth_full3_kernel<NN, true>), (int)C::SMEM);
-    if (e != cudaSuccess) return e;
+  auto run_int = [&]() -> cudaError_t {
+    if (g.n_int <= 0) return cudaSuccess;
+    cudaError_t ee = smem_opt_in(reinterpret_cast<const void*>(smooth_full3_kernel<NN, true>), (int)C::SMEM);
+    if (ee != cudaSuccess) return ee;
     dim3 grid((unsigned)((g.n_int + C::PPC - 1) / C::PPC), h->prm.nrhs);
-    smooth_full3_kernel<NN, true><<<grid, C::THREADS, C::SMEM, s>>>(ops, colour, r, x, N, nd, g);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (g.n_bnd > 0) {
-    e = smem_opt_in(reinterpret_cast<const void*>(smooth_full3_kernel<NN, false>), (int)C::SMEM);
-    if (e != cudaSuccess) return e;
+    return launch_prio(smooth_full3_kernel<NN, true>, grid, C::THREADS, C::SMEM, s, !h->bnd_first, h->prio_hi, ops,
+                       colour, r, x, N, nd, g);
+  };
+  auto run_bnd = [&]() -> cudaError_t {
+    if (g.n_bnd <= 0) return cudaSuccess;
+    cudaError_t ee = smem_opt_in(reinterpret_cast<const void*>(smooth_full3_kernel<NN, false>), (int)C::SMEM);
+    if (ee != cudaSuccess) return ee;
     dim3 grid((unsigned)((g.n_bnd + C::PPC - 1) / C::PPC), h->prm.nrhs);
-    smooth_full3_kernel<NN, false><<<grid, C::THREADS, C::SMEM, sb>>>(ops, colour, r, x, N, nd, g);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+    return launch_prio(smooth_full3_kernel<NN, false>, grid, C::THREADS, C::SMEM, sb, h->bnd_first, h->prio_hi, ops,
+                       colour, r, x, N, nd, g);
+  };
+  if ((e = h->bnd_first ? run_bnd() : run_int()) != cudaSuccess) return e;
+  if ((e = h->bnd_first ? run_int() : run_bnd()) != cudaSuccess) return e;
   if (fork) {
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, h->ev_join, 0)) != cudaSuccess) return e;

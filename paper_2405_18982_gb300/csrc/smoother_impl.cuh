@@ -31,6 +31,7 @@
 #pragma once
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "tensor_ops.cuh"
 
