@@ -230,8 +230,10 @@ sipg_status sipg_solve_zero(sipg_handle* h, const double* b, double* x, double r
 sipg_status sipg_adjoint_solve(sipg_handle* h, const double* g, double* lambda, double rtol,
                                int maxit, sipg_info* info, void* stream);
 /* Same as sipg_solve with HOST buffers f (nodal source, FP64, nrhs columns)
- * and u (solution): copies f in, forms b = M_h f, solves from x = 0, copies u
- * out, all on `stream`.  Synchronises stream. */
+ * and u (solution): copies f in, forms b = M_h f, solves from x = 0 on
+ * `stream`, and copies u out on a second stream of its own as soon as the
+ * iteration ends, beside the final true residual (a restart waits for that
+ * copy and the final x is copied again).  Synchronises both. */
 sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host, double rtol,
                             int maxit, sipg_info* info, void* stream);
 

@@ -226,7 +226,7 @@ class SIPG:
         return SolveInfo(info.iterations, info.status, info.rel_residual, info.nu,
                          [hist[i] for i in range(info.history_len)])
 
-    def solve_host(self, f_host, u_host, rtol=1e-10, maxit=200, stream=None, history=256):
+    def solve_host(self, f_host, u_host, rtol=1e-10, maxit=200, stream=None, history=256, allow_noconv=False):
         """f_host, u_host: CPU float64 tensors (pinned for async copies)."""
         if f_host.is_cuda or u_host.is_cuda:
             raise ValueError("solve_host takes host tensors")
@@ -235,7 +235,8 @@ class SIPG:
         st = self.lib.sipg_solve_host(self.h, ctypes.c_void_p(f_host.data_ptr()),
                                       ctypes.c_void_p(u_host.data_ptr()), rtol, maxit, ctypes.byref(info),
                                       self._stream(stream))
-        self._check(st)
+        if st != 0 and not (allow_noconv and st == B.SIPG_ENOCONV):
+            self._check(st)
         return SolveInfo(info.iterations, info.status, info.rel_residual, info.nu,
                          [hist[i] for i in range(info.history_len)])
 

@@ -241,7 +241,25 @@ struct FcgRun {
   sipg_status result = SIPG_OK;
   std::vector<double> hist;
   bool zero_start = false;  // x = 0 on entry: the first residual is b
+  // optional copy of x to host memory overlapped with the final true
+  // residual: issued on out_stream as soon as the iteration ends; a restart
+  // waits for it before it changes x, and marks it stale
+  double* out_host = nullptr;
+  size_t out_bytes = 0;
+  cudaStream_t out_stream = nullptr;
+  cudaEvent_t out_ready = nullptr, out_done = nullptr;
+  bool out_valid = false;  // the copy in flight holds the x the run ends with
 };
+
+sipg_status copy_out(FcgRun& r) {
+  sipg_handle* h = r.h;
+  SIPG_CHECK(cudaEventRecord(r.out_ready, r.s), "event record");
+  SIPG_CHECK(cudaStreamWaitEvent(r.out_stream, r.out_ready, 0), "stream wait");
+  SIPG_CHECK(cudaMemcpyAsync(r.out_host, r.x, r.out_bytes, cudaMemcpyDeviceToHost, r.out_stream), "D2H");
+  SIPG_CHECK(cudaEventRecord(r.out_done, r.out_stream), "event record");
+  r.out_valid = true;
+  return SIPG_OK;
+}
 
 bool run_any(const sipg_handle* h, bool (*pred)(const KrylovScalars&)) {
   for (int c = 0; c < h->prm.nrhs; ++c)
@@ -301,6 +319,10 @@ sipg_status advance(FcgRun& r) {
         r.phase = FcgRun::DONE;
         return SIPG_OK;
       }
+      if (r.out_valid) {  // x changes again: the copy in flight is stale
+        SIPG_CHECK(cudaStreamWaitEvent(r.s, r.out_done, 0), "stream wait");
+        r.out_valid = false;
+      }
       st = precondition(h, 1, r.s);  // z_0 = B r_0, p_0 = z_0
       if (st) return st;
       st = step_update(h, r.x, r.s);
@@ -324,6 +346,10 @@ sipg_status advance(FcgRun& r) {
         return queue_scalars(r);
       }
       r.phase = FcgRun::VERIFY;
+      if (r.out_host) {
+        st = copy_out(r);
+        if (st) return st;
+      }
       return launch_true_residual(r);
     case FcgRun::DONE:
       return SIPG_OK;
@@ -406,8 +432,13 @@ sipg_status drive(std::vector<FcgRun>& runs) {
   return SIPG_OK;
 }
 
+// out_host: also copy the final x there (out_stream, events: see FcgRun);
+// on return *out_copied says whether a copy of the final x was issued (the
+// caller then waits for out_stream, else copies x itself).
 sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, int maxit,
-                      sipg_info* info, cudaStream_t s, bool zero_start = false) {
+                      sipg_info* info, cudaStream_t s, bool zero_start = false, double* out_host = nullptr,
+                      cudaStream_t out_stream = nullptr, cudaEvent_t out_ready = nullptr,
+                      cudaEvent_t out_done = nullptr, bool* out_copied = nullptr) {
   h->rtol2 = rtol * rtol;
   std::vector<FcgRun> runs(1);
   runs[0].zero_start = zero_start;
@@ -417,7 +448,15 @@ sipg_status fcg_solve(sipg_handle* h, const double* b, double* x, double rtol, i
   runs[0].s = s;
   runs[0].maxit = maxit;
   runs[0].info = info;
+  if (out_host) {
+    runs[0].out_host = out_host;
+    runs[0].out_bytes = h->lv[h->L].ndofs * h->prm.nrhs * sizeof(double);
+    runs[0].out_stream = out_stream;
+    runs[0].out_ready = out_ready;
+    runs[0].out_done = out_done;
+  }
   sipg_status st = drive(runs);
+  if (out_copied) *out_copied = runs[0].out_valid;
   if (st) return st;
   return finish(runs[0]);
 }
@@ -1267,10 +1306,31 @@ sipg_status sipg_solve_host(sipg_handle* h, const double* f_host, double* u_host
   SIPG_CHECK(cudaMemcpyAsync(dx, f_host, bytes, cudaMemcpyHostToDevice, s), "H2D");
   SIPG_CHECK(launch_mass(h, dx, db, s), "mass");
   h->launches += 1;
-  sipg_status r = fcg_solve(h, db, dx, rtol, maxit, info, s, true);
+  // the copy of u back to the host runs beside the final true residual (a
+  // second stream of this call)
+  cudaStream_t os = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
+  auto release = [&]() {
+    if (os) cudaStreamDestroy(os);
+    if (ready) cudaEventDestroy(ready);
+    if (done) cudaEventDestroy(done);
+  };
+  if (cudaStreamCreateWithFlags(&os, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+    release();
+    return fail(h, SIPG_ECUDA, "stream or event creation");
+  }
+  bool copied = false;
+  sipg_status r = fcg_solve(h, db, dx, rtol, maxit, info, s, true, u_host, os, ready, done, &copied);
+  cudaError_t e = cudaStreamSynchronize(os);  // a copy in flight ends before x or u goes
+  if (r == SIPG_OK || r == SIPG_ENOCONV) {
+    if (e == cudaSuccess && !copied) e = cudaMemcpyAsync(u_host, dx, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  release();
   if (r != SIPG_OK && r != SIPG_ENOCONV) return r;
-  SIPG_CHECK(cudaMemcpyAsync(u_host, dx, bytes, cudaMemcpyDeviceToHost, s), "D2H");
-  SIPG_CHECK(cudaStreamSynchronize(s), "sync");
+  if (e != cudaSuccess) return cuda_fail(h, e, "D2H");
   return r;
 }
 

@@ -297,17 +297,36 @@ def test_multi_rhs_and_graphs(monkeypatch):
             assert np.array_equal(got, ref)
 
 
-def test_solve_host_roundtrip():
+@pytest.mark.parametrize("case", [(2, 3, 4, 3, 0, 1, True), (3, 3, 4, 3, 1, 2, True), (3, 2, 3, 2, 1, 1, False)],
+                         ids=["2d", "3d-graphs-2rhs", "3d-pageable"])
+def test_solve_host_roundtrip(case):
+    # host f in, host u out; the copy of u overlaps the final true residual
+    # (second stream), so u must be the final x for every column; also with
+    # pageable host memory and with a step limit that ends the solve early
     import torch
-    dim, k, l2, nl = 2, 3, 4, 3
+    dim, k, l2, nl, graphs, nrhs, pinned = case
     N = 1 << l2
-    s = make(dim, k, l2, nl, prec=SIPG_FP32)
-    f = inputs.normal(930, s.ndofs())
-    fh = torch.tensor(f, dtype=torch.float64).pin_memory()
-    uh = torch.zeros_like(fh).pin_memory()
+    s = make(dim, k, l2, nl, prec=SIPG_FP32, graphs=graphs, nrhs=nrhs)
+    n = s.ndofs()
+    f = np.concatenate([inputs.normal(930 + c, n) for c in range(nrhs)])
+    fh = torch.tensor(f, dtype=torch.float64)
+    uh = torch.zeros_like(fh)
+    if pinned:
+        fh, uh = fh.pin_memory(), uh.pin_memory()
     info = s.solve_host(fh, uh, rtol=1e-12)
-    u = GlobalFD(dim, k, N).solve(rhs_from_nodal(dim, k, N, f))
-    assert rel_inf(uh.numpy(), u) < 1e-8
+    assert info.rel_residual <= 1e-12
+    for c in range(nrhs):
+        u = GlobalFD(dim, k, N).solve(rhs_from_nodal(dim, k, N, f[c * n:(c + 1) * n]))
+        assert rel_inf(uh.numpy()[c * n:(c + 1) * n], u) < 1e-8
+    # two steps only: u is the iterate the device holds after them
+    uh2 = torch.zeros_like(fh)
+    info2 = s.solve_host(fh, uh2, rtol=1e-14, maxit=2, allow_noconv=True)
+    assert info2.iterations == 2
+    xd = torch.zeros(nrhs, n, dtype=torch.float64, device="cuda")
+    bd = torch.zeros_like(xd)
+    s.rhs(torch.from_numpy(f).to("cuda").view(nrhs, n), bd)
+    s.solve(bd, xd, rtol=1e-14, maxit=2, allow_noconv=True, zero_start=True)
+    assert np.array_equal(uh2.numpy(), host(xd).ravel())
 
 
 def test_dot_and_edge_cases():
